@@ -1,0 +1,345 @@
+"""Throughput benchmark of the RKDG + CSWENO step on one GB300 (or N, as
+independent replicas).
+
+Workload: the Mach-10 double-Mach-reflection set-up of the paper's Example 5
+on [0,4]x[0,1], jittered split-square mesh 960x240 (460,800 triangles),
+Euler P2 (24 modal DOF per cell), KXRCF detection with C_K = 1, CSWENO
+reconstruction of flagged cells, SSP-RK3, CFL 0.1; FP32 bulk arithmetic with
+the smoothness-indicator sums, nonlinear weights, troubled-cell test and
+positivity check in FP64.  A step is one SSP-RK3 time step (three stages,
+each: operator + RK update, detection, reconstruction, write-back) plus the
+CFL reduction.
+
+Metric: element-DOF x RK-stage updates per second = cells * 24 * 3 * steps / s.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (a fixed random subset of cells of the full mesh) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2106_06280_gb300 import workloads as W  # noqa: E402
+
+METRIC = "element-DOF x RK-stage updates/s"
+UNIT = "DOF-stage/s"
+NX, NY, K = 960, 240, 2
+NP, NV = 6, 4
+WORKLOAD = "double Mach reflection, Euler P2, jittered split-square 960x240 (460,800 triangles), KXRCF + CSWENO, SSP-RK3, CFL 0.1"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lr
+
+
+def stage_bytes_per_cell(fp32: bool) -> float:
+    """Algorithmic DRAM bytes of the operator + RK stage kernel per cell,
+    averaged over the three stages: read u^(i-1) (S), write u^(i) (S), read u^n
+    (S, stages 2 and 3), geometry (4 inverse-Jacobian + 9 scaled-normal words),
+    three neighbour indices (12 B) and the packed neighbour faces (1 B).
+    Neighbour traces are reuse of data already counted."""
+    s = 4 if fp32 else 8
+    S = NP * NV * s
+    geo = 13 * s + 12 + 1
+    return (3 * (2 * S + geo) + 2 * S) / 3.0
+
+
+def read_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for key in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if key in d:
+                    return float(d[key]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("operator.cu", "physics.cuh", "common.cuh", "tables.cuh", "rules.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2106_06280_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(khash):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_stage_euler_p2_dmr.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != khash:
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, dev):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9 or f[0] != str(dev):
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_solver(csw, precision, stream, seed=3):
+    pb = W.double_mach(NX, NY, seed=seed)
+    s = csw.Solver(csw.EULER, K, precision, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=stream)
+    s.setup(pb)
+    s.project_ic(pb.u0, apply_limiter=2)
+    return pb, s
+
+
+def run_ours(args):
+    import torch
+
+    ws, rk, lr = dist_info()
+    torch.cuda.set_device(lr)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2106_06280_gb300 import build as B
+    B.build()
+    from paper_2106_06280_gb300 import cswdg as csw
+
+    stream = torch.cuda.current_stream().cuda_stream
+    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk)
+    nc = pb.mesh.nc
+    t_end = pb.t_end
+    s.step(0.0, args.warmup, t_end)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler()
+    if rk == 0:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.step(0.0, args.steps, t_end)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop(lr) if rk == 0 else None
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = float(nc) * NP * NV * 3 * args.steps * ws
+    value = units / (ms * 1e-3)
+    nflag = s.num_flagged()
+
+    # per-kernel device time (events after every launch, no graph), same state trajectory
+    prof, nl = s.profile_step(0.0, args.profile_steps, t_end)
+    stage_ms = prof["stage"] / (3 * args.profile_steps)
+    bpc = stage_bytes_per_cell(True)
+    achieved = nc * bpc / (stage_ms * 1e-3) / 1e9
+    peak, peak_src = read_peak()
+    khash = kernel_hash()
+    traffic = read_traffic(khash)
+
+    # end to end: pinned host state in, one step, state out, through the C interface
+    host_in = torch.empty((nc, NV, NP), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((nc, NV, NP), dtype=torch.float64, pin_memory=True).numpy()
+    s.read_modes(host_in)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.write_modes(host_in)
+        s.step(0.0, 1, t_end)
+        s.read_modes(host_out)
+    t1 = time.perf_counter()
+    e2e_value = float(nc) * NP * NV * 3 * e2e_steps * ws / (t1 - t0)
+
+    # FP64 mode on the same workload (secondary)
+    fp64 = None
+    if args.fp64_steps > 0:
+        s.close()
+        pb64, s64 = setup_solver(csw, csw.FP64, stream, seed=3 + rk)
+        s64.step(0.0, 1, t_end)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        s64.step(0.0, args.fp64_steps, t_end)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        fp64 = {"value": float(nc) * NP * NV * 3 * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+        s64.close()
+
+    if rk != 0:
+        return None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": nc, "degree": K, "dof_per_cell": NP * NV,
+                   "precision": "FP32 bulk; FP64 smoothness-indicator sums, nonlinear weights, KXRCF test, positivity",
+                   "limiter": "KXRCF C_K=1 + CSWENO", "initial_condition": "L2 projection, every cell reconstructed once",
+                   "l2": "inputs larger than L2: per-step working set about 200 MB (three 44 MB state arrays, 24 MB geometry, operator blocks of flagged cells) > 129 MB L2",
+                   "replicas": "one independent copy of the workload per GPU" if ws > 1 else None,
+                   "flagged_cells_last_pass": nflag},
+        "roofline": {"bound": "hbm", "kernel": "k_stage (operator + RK update)", "achieved": achieved, "peak": peak,
+                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "bytes_per_cell_algorithmic": bpc, "stage_ms": stage_ms,
+                     "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()}},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nc * NV * NP * 8,
+                "d2h_bytes_per_step": nc * NV * NP * 8, "steps": e2e_steps,
+                "path": "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)"},
+        "gpu_launches": s.launches_per_step(True) * args.steps,
+        "clocks": clk,
+        "fp64": fp64,
+    }
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    s.close()
+    return out
+
+
+def cpu_baseline(sample, seed=3):
+    """The FP64 oracle as it stands, single thread, on a fixed random sample of
+    the cells of the same mesh and initial state: one SSP-RK3 step's work on
+    the sample = 3 x (operator on the sample + KXRCF on the sample +
+    reconstruction of the flagged sample cells)."""
+    import oracle
+    pb = W.double_mach(NX, NY, seed=seed)
+    o = oracle.Oracle(pb, k=K, limiter=1)
+    oa = oracle.Oracle(pb, k=K, limiter=2)
+    rng = np.random.default_rng(12345)
+    cells = np.sort(rng.choice(pb.mesh.nc, size=sample, replace=False)).astype(np.int32)
+    nb, _, _ = o.connectivity()
+    near = np.unique(np.concatenate([cells, nb[cells].ravel()]))
+    near = near[near >= 0]
+    nb2 = nb[near].ravel()
+    near2 = np.unique(np.concatenate([near, nb2[nb2 >= 0]])).astype(np.int32)
+    u = np.zeros((pb.mesh.nc, NV, NP))
+    o.project_cells(pb.u0, near2, u)
+    lim, _ = oa.limit_cells(u, near)
+    u[near] = lim
+    t0 = time.perf_counter()
+    nflag = 0
+    for _ in range(3):
+        o.rhs_cells(u, cells)
+        fl, _ = o.detect_cells(u, cells)
+        flagged = cells[fl.astype(bool)]
+        nflag += len(flagged)
+        if len(flagged):
+            o.limit_cells(u, flagged)
+    dt = time.perf_counter() - t0
+    return {"value": sample * NP * NV * 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample} random cells of the 460,800-cell mesh at the initial state, one SSP-RK3 step's work "
+                      f"(3 x operator + KXRCF on the sample, CSWENO on its flagged cells: {nflag // 3} per stage); "
+                      f"{dt:.1f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    ws, rk, lr = dist_info()
+    if rk != 0:
+        return None
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    t0 = time.perf_counter()
+    cb = None
+    for _ in range(max(1, args.steps)):
+        cb = cpu_baseline(args.ref_sample)
+        vals.append(cb["value"])
+    t1 = time.perf_counter()
+    value = float(np.median(vals))
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * (t1 - t0) / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "cells": NX * NY * 2, "degree": K},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=200000)
+    ap.add_argument("--ref-sample", type=int, default=4000)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * cswdg.h -- C interface of the GB300 (sm_103a) RKDG + compact subcell WENO
+ * (CSWENO) solver for 2D Burgers and 2D Euler on unstructured triangles,
+ * after Kochi & Ramakrishna, arXiv 2106.06280.
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a cswdg_status; nothing throws or aborts across
+ *    the interface.  On failure cswdg_last_error() gives a one-line reason.
+ *  - Pointers named *_host are host memory owned by the caller, read or
+ *    written only during the call.  Pointers named *_dev are device memory
+ *    owned by the caller.  The library owns every other device buffer.
+ *  - Cell-indexed arrays are in the caller's cell order (the order of `tri`
+ *    in cswdg_mesh_upload); the library reorders cells internally for
+ *    locality and undoes it on every read.
+ *  - Modal arrays are double, laid out modes[(c*nvar + v)*np + m] for cell c,
+ *    variable v (Burgers: u; Euler: rho, rho u, rho v, E) and mode m < np =
+ *    (k+1)(k+2)/2, as coefficients of the physically orthonormal basis
+ *    psi^K_m(x) = sqrt(2/|K|) psi_m(r(x)), where psi_m is the orthonormal
+ *    Dubiner basis on the reference triangle {r,s >= -1, r+s <= 0}
+ *    (Sec. 2, Eq. triangleBasis; mode order of the index m there) and r(x)
+ *    the affine map taking the triangle's vertices tri[3c], tri[3c+1],
+ *    tri[3c+2] to (-1,-1), (1,-1), (-1,1).  The local mass matrix
+ *    (Eq. massMatrix2D) is then the identity and the cell mean is
+ *    modes[.., 0] / sqrt(|K|).
+ *  - Work is issued on cswdg_config.stream (NULL: the legacy default
+ *    stream).  Calls that return host data synchronise that stream.
+ *  - A solver is not thread-safe; distinct solvers are independent.
+ */
+#ifndef CSWDG_H
+#define CSWDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cswdg_solver cswdg_solver;
+
+typedef enum {
+    CSWDG_OK = 0,
+    CSWDG_EINVAL = 1,    /* bad argument or call order */
+    CSWDG_ECUDA = 2,     /* CUDA runtime error */
+    CSWDG_EMESH = 3,     /* non-conforming mesh, unpaired periodic face, missing tag */
+    CSWDG_ENONPHYS = 4,  /* Euler cell mean with rho <= 0 or p <= 0, or a NaN */
+    CSWDG_ELSQ = 5,      /* rank-deficient stencil least squares at set-up */
+    CSWDG_ETIMEOUT = 6,  /* reserved: bounded device wait expired */
+    CSWDG_ENOMEM = 7     /* device allocation failed */
+} cswdg_status;
+
+enum { CSWDG_BURGERS = 0, CSWDG_EULER = 1 };
+enum { CSWDG_FP64 = 0, CSWDG_FP32_BULK = 1 };
+enum { CSWDG_LIMITER_OFF = 0, CSWDG_LIMITER_KXRCF = 1, CSWDG_LIMITER_ALL = 2 };
+/* Boundary kinds, cswdg_set_boundary. */
+enum {
+    CSWDG_BC_PERIODIC = 0,     /* paired by translation (mesh_upload `period`) */
+    CSWDG_BC_DIRICHLET = 1,    /* params: nvar constant conserved values */
+    CSWDG_BC_TRANSMISSIVE = 2, /* ghost = interior trace */
+    CSWDG_BC_WALL = 3,         /* Euler: interior trace with the normal momentum reversed */
+    CSWDG_BC_SHOCKLINE = 4     /* params: x0, cot, speed, A[nvar], B[nvar];
+                                  ghost = A where x < x0 + y*cot + speed*t, else B */
+};
+
+typedef struct {
+    int32_t equation;  /* CSWDG_BURGERS (Eq. 2dBurgers) or CSWDG_EULER (Eq. 2dEulerEquations) */
+    int32_t degree;    /* k in {1, 2}: P^k DG, np = (k+1)(k+2)/2 (Sec. 2) */
+    int32_t precision; /* CSWDG_FP64: every step in double.  CSWDG_FP32_BULK: state,
+                          operator and RK update in float with float accumulation;
+                          the troubled-cell test, the smoothness-indicator sums,
+                          the nonlinear weights and the positivity check in double */
+    int32_t limiter;   /* CSWDG_LIMITER_*: off, KXRCF-detected cells (Sec. 3.1), every cell */
+    double c_k;        /* KXRCF threshold C_K (Sec. 3.1 takes 1) */
+    double cfl;        /* time-step factor of the CFL rule used when dt <= 0 */
+    double gamma;      /* ratio of specific heats (1.4) */
+    void *stream;      /* cudaStream_t, or NULL */
+} cswdg_config;
+
+/* Create a solver.  Allocates nothing on the device until mesh upload.
+ * Errors: EINVAL (unsupported equation/degree/precision/limiter). */
+cswdg_status cswdg_create(const cswdg_config *cfg, cswdg_solver **out);
+
+/* Free every device and host resource of the solver (NULL is a no-op). */
+void cswdg_destroy(cswdg_solver *s);
+
+/* One-line description of the last error of this solver (never NULL). */
+const char *cswdg_last_error(const cswdg_solver *s);
+
+/* Boundary kind and parameters of a face tag (0 <= tag < 16).  Must precede
+ * cswdg_mesh_upload for every tag the mesh uses.  Errors: EINVAL. */
+cswdg_status cswdg_set_boundary(cswdg_solver *s, int32_t tag, int32_t kind,
+                                const double *params_host, int32_t nparams);
+
+/* Upload a conforming straight-sided triangulation (Sec. 2, Eq. triangulation).
+ *   xy_host[2*nv]        vertex coordinates
+ *   tri_host[3*nc]       counter-clockwise vertex indices per triangle
+ *   bface_host[3*nbf]    every boundary edge as (v0, v1, tag)
+ *   period_host[2]       (Lx, Ly) translations pairing CSWDG_BC_PERIODIC faces, or NULL
+ * Builds faces, neighbours, periodic pairs, a Morton locality order, per-cell
+ * geometry, and (limiter on) the per-cell stencil operators of the CSWENO
+ * reconstruction on the device.  Sets t = 0 and a zero state.
+ * Errors: EINVAL, EMESH, ELSQ, ENOMEM, ECUDA. */
+cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy_host,
+                               int64_t nc, const int32_t *tri_host,
+                               int64_t nbf, const int32_t *bface_host,
+                               const double *period_host);
+
+/* Number of volume-quadrature points per cell (3 for k=1, 7 for k=2). */
+int32_t cswdg_num_ic_points(const cswdg_solver *s);
+
+/* Physical coordinates of the volume-quadrature points:
+ * xy_host[(c*Q + q)*2 + {0,1}], Q = cswdg_num_ic_points. */
+cswdg_status cswdg_ic_points(cswdg_solver *s, double *xy_host);
+
+/* L2 projection of initial values given at those points,
+ * values_host[(c*Q + q)*nvar + v], onto the modes.  apply_limiter: 0 none;
+ * 1 one pass of the configured limiter at t = 0; 2 one pass reconstructing
+ * every cell (for discontinuous data, whose projection can leave negative
+ * density or pressure inside cells the detector does not flag).  The
+ * limiter runs only when the solver was created with a limiter.
+ * Errors: EINVAL, ENONPHYS, ECUDA. */
+cswdg_status cswdg_project_ic(cswdg_solver *s, const double *values_host, int32_t apply_limiter);
+
+/* Advance nsteps SSP-RK3 steps (Sec. 3.2, Eq. timeIntegrate, Table tvd: third
+ * order), the limiter after every stage.  dt > 0: fixed step; dt <= 0: the
+ * CFL rule dt = cfl * min_K r_K / max_K lambda_K (r_K the inradius, lambda_K
+ * the largest wave speed of the cell mean).  Steps are clipped so that t never
+ * passes t_end; once t == t_end further steps do nothing.  The steps run as a
+ * CUDA graph.  t_out_host (nullable) receives the time reached.
+ * Errors: EINVAL, ENONPHYS, ECUDA. */
+cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *t_out_host);
+
+/* The same steps launched one kernel at a time (no graph) with a CUDA event
+ * after every launch; ms_host[5] receives the summed device time of each
+ * kernel class: [0] CFL reduction + step begin, [1] operator + RK stage,
+ * [2] KXRCF detection, [3] CSWENO reconstruction, [4] write-back of the
+ * reconstructed modes.  launches_host (nullable): kernels launched.
+ * Advances the state like cswdg_step.  Errors: EINVAL, ENONPHYS, ECUDA. */
+cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end,
+                                double *ms_host, int64_t *launches_host);
+
+/* Kernels one cswdg_step step launches (use_cfl: dt <= 0). */
+int32_t cswdg_launches_per_step(const cswdg_solver *s, int32_t use_cfl);
+
+/* Current time; set the time (e.g. after restoring a checkpoint). */
+cswdg_status cswdg_get_time(cswdg_solver *s, double *t_host);
+cswdg_status cswdg_set_time(cswdg_solver *s, double t);
+
+/* Read / write the modal state (layout above, nc*nvar*np doubles).
+ * Together with cswdg_set_time this is a full checkpoint. */
+cswdg_status cswdg_read_modes(cswdg_solver *s, double *modes_host);
+cswdg_status cswdg_write_modes(cswdg_solver *s, const double *modes_host);
+
+/* Troubled-cell flags of the last limiter pass (1 byte per cell, 0 or 1);
+ * with the limiter off all zero. */
+cswdg_status cswdg_read_flags(cswdg_solver *s, uint8_t *flags_host);
+
+/* Number of cells flagged by the last limiter pass. */
+cswdg_status cswdg_num_flagged(cswdg_solver *s, int64_t *n_host);
+
+/* sum_K |K| * mean_K per variable (nvar doubles). */
+cswdg_status cswdg_conservation(cswdg_solver *s, double *sums_host);
+
+/* The semi-discrete operator alone (Sec. 2, Eq. weakFormScheme2D with the
+ * local Lax-Friedrichs flux of Sec. 2 and M = I): rhs = L_h(u) at time t for
+ * the given modes.  Replaces the solver state by modes_in.
+ * Errors: EINVAL, ECUDA. */
+cswdg_status cswdg_eval_rhs(cswdg_solver *s, double t, const double *modes_in_host, double *rhs_host);
+
+/* One limiter pass alone (Sec. 3.1 detection, or every cell, then Sec. 3.2
+ * reconstruction of the flagged cells) at time t: the solver state becomes
+ * the limited modes_in; modes_out_host and flags_host (both nullable) receive
+ * the result.  Errors: EINVAL, ENONPHYS, ECUDA. */
+cswdg_status cswdg_limit(cswdg_solver *s, double t, const double *modes_in_host,
+                         double *modes_out_host, uint8_t *flags_host);
+
+/* Time step the CFL rule gives for the current state (no clipping). */
+cswdg_status cswdg_cfl_dt(cswdg_solver *s, double *dt_host);
+
+/* Device-pointer variant of one SSP-RK3 stage for callers that manage their
+ * own buffers: out = a*un + b*(uprev + dt*L_h(uprev)) at time t_rhs, in the
+ * library's internal layout (see cswdg_internal_layout) and precision.
+ * un_dev may be NULL when a == 0.  No limiter.  Errors: EINVAL, ECUDA. */
+cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un_dev, const void *uprev_dev, void *out_dev,
+                             double a, double b, double dt, double t_rhs);
+
+/* Internal layout of device state arrays: element (v, m, cell i) at
+ * [(v*np + m)*ldc + i] of the precision's type (double in FP64, float in
+ * FP32_BULK), internal cell i = perm_host[user cell]; ldc >= nc.  Coefficients
+ * are sqrt(2/|K|) times the user modes (the reference-orthonormal basis).
+ * perm_host (nullable) receives nc int32 user->internal indices. */
+cswdg_status cswdg_internal_layout(cswdg_solver *s, int64_t *ldc_host, int32_t *perm_host);
+
+/* Diagnostic: the per-cell CSWENO operator block of a user cell as built at
+ * mesh upload (subcell-mean weights, least-squares pseudo-inverses,
+ * smoothness-indicator factor, gradient maps, projection, mean side length;
+ * layout of Ops<K> in csrc/kernels.h).  *n receives its length (0 with the
+ * limiter off); out (nullable) receives the values as doubles. */
+cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out_host, int32_t *n_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSWDG_H */

@@ -1,0 +1,719 @@
+// api.cu -- the C interface (include/cswdg.h): solver object, mesh upload
+// (connectivity, periodic pairing, Morton locality order, geometry), device
+// memory, the SSP-RK3 step as a captured CUDA graph, and read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/cswdg.h"
+#include "kernels.h"
+#include "mesh_host.cuh"
+#include "rules.cuh"
+#include "tables.cuh"
+
+using namespace csw;
+
+struct cswdg_solver {
+    cswdg_config cfg{};
+    int nv = 1, np = 3, k = 1, eq = 0, fp32 = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    BcTab bc{};
+    bool mesh_ready = false;
+    int nc = 0, ldc = 0, nbfaces = 0;
+    double rmin = 0.0;
+    std::vector<int32_t> perm;     // internal -> user
+    std::vector<int32_t> iperm;    // user -> internal
+    std::vector<double> vtx_user;  // 6 per user cell (for IC points)
+    // device
+    void *U = nullptr, *A = nullptr, *B = nullptr;  // state arrays
+    void *geo = nullptr;
+    int32_t *nbr = nullptr;
+    uint8_t *nbf = nullptr;
+    BFace *bf = nullptr;
+    BcTab *bcd = nullptr;
+    int32_t *dperm = nullptr;
+    double *sc = nullptr, *area = nullptr;
+    void *ops = nullptr;
+    uint8_t *flags = nullptr, *flags_user = nullptr;
+    int32_t *flist = nullptr;
+    void *lim_out = nullptr;
+    Ctl *ctl = nullptr;
+    double *dev_user = nullptr, *cons_part = nullptr, *cons_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int lim_grid = 1;
+};
+
+namespace {
+
+cswdg_status fail(cswdg_solver *s, cswdg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(s, CSWDG_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T> cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, std::max<size_t>(n, 1) * sizeof(T));
+}
+
+bool tables_ready = false;
+
+template <typename R> MeshDev<R> mesh_dev(const cswdg_solver *s)
+{
+    MeshDev<R> M;
+    M.nc = s->nc;
+    M.ldc = s->ldc;
+    M.geo = (const R *)s->geo;
+    M.nbr = s->nbr;
+    M.nbf = s->nbf;
+    M.bf = s->bf;
+    M.bc = s->bcd;
+    M.gamma = s->cfg.gamma;
+    return M;
+}
+
+void free_device(cswdg_solver *s)
+{
+    for (int i = 0; i < 2; ++i)
+        if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
+    void *ptrs[] = {s->U, s->A, s->B, s->geo, s->nbr, s->nbf, s->bf, s->bcd, s->dperm, s->sc, s->area, s->ops, s->flags,
+                    s->flags_user, s->flist, s->lim_out, s->ctl, s->dev_user, s->cons_part, s->cons_out};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    s->U = s->A = s->B = s->geo = s->ops = s->lim_out = nullptr;
+    s->nbr = s->flist = s->dperm = nullptr;
+    s->nbf = s->flags = s->flags_user = nullptr;
+    s->bf = nullptr;
+    s->bcd = nullptr;
+    s->sc = s->area = s->dev_user = s->cons_part = s->cons_out = nullptr;
+    s->ctl = nullptr;
+    s->mesh_ready = false;
+}
+
+// ---------------------------------------------------------------------------
+// launch sequences.  `prof` (nullable) collects one event after every kernel
+// launch, tagged with its kernel class, for cswdg_profile_step.
+// ---------------------------------------------------------------------------
+enum { KC_CFL = 0, KC_STAGE = 1, KC_DETECT = 2, KC_LIMIT = 3, KC_SCATTER = 4, KC_COUNT = 5 };
+struct Prof {
+    std::vector<std::pair<int, cudaEvent_t>> ev;
+};
+
+void mark(Prof *prof, int cls, cudaStream_t st)
+{
+    if (!prof) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    prof->ev.push_back({cls, e});
+}
+
+cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st, Prof *prof = nullptr, bool force_all = false)
+{
+    if (s->cfg.limiter == CSWDG_LIMITER_OFF) return CSWDG_OK;
+    const int all = (s->cfg.limiter == CSWDG_LIMITER_ALL) || force_all;
+    CK(cudaMemsetAsync(&s->ctl->nflag, 0, sizeof(int32_t), st));
+    if (s->fp32) {
+        MeshDev<float> M = mesh_dev<float>(s);
+        launch_detect<float>(s->eq, s->k, M, (const float *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        mark(prof, KC_DETECT, st);
+        launch_limit<float>(s->eq, s->k, M, (const float *)u, (const float *)s->ops, s->flist, s->ctl, tfac, (float *)s->lim_out,
+                            s->lim_grid, st);
+        mark(prof, KC_LIMIT, st);
+        launch_scatter<float>(s->nv, s->np, s->ldc, s->flist, (const float *)s->lim_out, (float *)u, s->ctl, s->lim_grid, st);
+        mark(prof, KC_SCATTER, st);
+    } else {
+        MeshDev<double> M = mesh_dev<double>(s);
+        launch_detect<double>(s->eq, s->k, M, (const double *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        mark(prof, KC_DETECT, st);
+        launch_limit<double>(s->eq, s->k, M, (const double *)u, (const double *)s->ops, s->flist, s->ctl, tfac,
+                             (double *)s->lim_out, s->lim_grid, st);
+        mark(prof, KC_LIMIT, st);
+        launch_scatter<double>(s->nv, s->np, s->ldc, s->flist, (const double *)s->lim_out, (double *)u, s->ctl, s->lim_grid, st);
+        mark(prof, KC_SCATTER, st);
+    }
+    CK(cudaGetLastError());
+    return CSWDG_OK;
+}
+
+cswdg_status stage(cswdg_solver *s, const void *un, const void *up, void *out, double a, double b, double cl, double tfac,
+                   cudaStream_t st, Prof *prof = nullptr)
+{
+    if (s->fp32) {
+        launch_stage<float>(s->eq, s->k, mesh_dev<float>(s), (const float *)un, (const float *)up, (float *)out, (float)a, (float)b,
+                            (float)cl, tfac, s->ctl, st);
+    } else {
+        launch_stage<double>(s->eq, s->k, mesh_dev<double>(s), (const double *)un, (const double *)up, (double *)out, a, b, cl, tfac,
+                             s->ctl, st);
+    }
+    mark(prof, KC_STAGE, st);
+    CK(cudaGetLastError());
+    return CSWDG_OK;
+}
+
+// One SSP-RK3 step (Table tvd): stage i evaluates L_h at t + (0, dt, dt/2)
+// and the limiter after it sees t + (dt, dt/2, dt).
+cswdg_status record_step(cswdg_solver *s, int use_cfl, cudaStream_t st, Prof *prof = nullptr)
+{
+    cswdg_status r;
+    if (use_cfl) {
+        if (s->fp32) launch_cfl<float>(s->eq, mesh_dev<float>(s), s->np, (const float *)s->U, s->ctl, st);
+        else launch_cfl<double>(s->eq, mesh_dev<double>(s), s->np, (const double *)s->U, s->ctl, st);
+    }
+    launch_begin_step(s->ctl, use_cfl, st);
+    mark(prof, KC_CFL, st);
+    CK(cudaGetLastError());
+    if ((r = stage(s, nullptr, s->U, s->A, 0.0, 1.0, 1.0, 0.0, st, prof))) return r;
+    if ((r = limiter_pass(s, s->A, 1.0, st, prof))) return r;
+    if ((r = stage(s, s->U, s->A, s->B, 0.75, 0.25, 0.25, 1.0, st, prof))) return r;
+    if ((r = limiter_pass(s, s->B, 0.5, st, prof))) return r;
+    if ((r = stage(s, s->U, s->B, s->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, st, prof))) return r;
+    if ((r = limiter_pass(s, s->U, 1.0, st, prof))) return r;
+    return CSWDG_OK;
+}
+
+cswdg_status get_graph(cswdg_solver *s, int use_cfl)
+{
+    if (s->graph[use_cfl]) return CSWDG_OK;
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(cap);
+        return fail(s, CSWDG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    }
+    cswdg_status r = record_step(s, use_cfl, cap);
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (r) { if (g) cudaGraphDestroy(g); return r; }
+    if (e != cudaSuccess) return fail(s, CSWDG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&s->graph[use_cfl], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(s, CSWDG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return CSWDG_OK;
+}
+
+cswdg_status read_ctl(cswdg_solver *s, Ctl *h)
+{
+    CK(cudaMemcpyAsync(h, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status write_ctl(cswdg_solver *s, const Ctl *h)
+{
+    CK(cudaMemcpyAsync(s->ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status check_err(cswdg_solver *s, Ctl *h)
+{
+    if (h->err & ERR_NONPHYS) {
+        Ctl c = *h;
+        c.err = 0;
+        write_ctl(s, &c);
+        return fail(s, CSWDG_ENONPHYS, "non-physical cell mean (rho <= 0, p <= 0 or NaN)");
+    }
+    return CSWDG_OK;
+}
+
+cswdg_status upload_modes(cswdg_solver *s, const double *modes, void *dst)
+{
+    const size_t n = (size_t)s->nc * s->nv * s->np;
+    CK(cudaMemcpyAsync(s->dev_user, modes, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (s->fp32) launch_from_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, s->dev_user, (float *)dst, s->stream);
+    else launch_from_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, s->dev_user, (double *)dst, s->stream);
+    CK(cudaGetLastError());
+    return CSWDG_OK;
+}
+
+cswdg_status download_modes(cswdg_solver *s, const void *src, double *modes)
+{
+    const size_t n = (size_t)s->nc * s->nv * s->np;
+    if (s->fp32) launch_to_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const float *)src, s->dev_user, s->stream);
+    else launch_to_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const double *)src, s->dev_user, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(modes, s->dev_user, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface
+// ===========================================================================
+extern "C" {
+
+cswdg_status cswdg_create(const cswdg_config *cfg, cswdg_solver **out)
+{
+    if (!cfg || !out) return CSWDG_EINVAL;
+    *out = nullptr;
+    if ((cfg->equation != CSWDG_BURGERS && cfg->equation != CSWDG_EULER) || (cfg->degree != 1 && cfg->degree != 2) ||
+        (cfg->precision != CSWDG_FP64 && cfg->precision != CSWDG_FP32_BULK) || cfg->limiter < 0 || cfg->limiter > 2 ||
+        !(cfg->gamma > 1.0))
+        return CSWDG_EINVAL;
+    cswdg_solver *s = new (std::nothrow) cswdg_solver();
+    if (!s) return CSWDG_ENOMEM;
+    s->cfg = *cfg;
+    s->eq = cfg->equation;
+    s->k = cfg->degree;
+    s->nv = (s->eq == CSWDG_EULER) ? 4 : 1;
+    s->np = (s->k + 1) * (s->k + 2) / 2;
+    s->fp32 = (cfg->precision == CSWDG_FP32_BULK);
+    s->stream = (cudaStream_t)cfg->stream;
+    for (int t = 0; t < CSW_MAXTAG; ++t) s->bc.kind[t] = -1;
+    if (!tables_ready) {
+        cudaError_t e = operator_upload_tables();
+        if (e == cudaSuccess) e = limiter_upload_tables();
+        if (e != cudaSuccess) {
+            delete s;
+            return CSWDG_ECUDA;
+        }
+        tables_ready = true;
+    }
+    *out = s;
+    return CSWDG_OK;
+}
+
+void cswdg_destroy(cswdg_solver *s)
+{
+    if (!s) return;
+    free_device(s);
+    delete s;
+}
+
+const char *cswdg_last_error(const cswdg_solver *s)
+{
+    if (!s) return "null solver";
+    return s->err.c_str();
+}
+
+cswdg_status cswdg_set_boundary(cswdg_solver *s, int32_t tag, int32_t kind, const double *params, int32_t nparams)
+{
+    if (!s) return CSWDG_EINVAL;
+    if (tag < 0 || tag >= CSW_MAXTAG || kind < 0 || kind > CSWDG_BC_SHOCKLINE || nparams < 0 || nparams > CSW_MAXPAR ||
+        (nparams > 0 && !params))
+        return fail(s, CSWDG_EINVAL, "bad boundary tag/kind/params");
+    const int need = (kind == CSWDG_BC_DIRICHLET) ? s->nv : (kind == CSWDG_BC_SHOCKLINE) ? 3 + 2 * s->nv : 0;
+    if (nparams < need) return fail(s, CSWDG_EINVAL, "boundary kind %d needs %d parameters", kind, need);
+    s->bc.kind[tag] = kind;
+    for (int i = 0; i < CSW_MAXPAR; ++i) s->bc.par[tag][i] = (i < nparams) ? params[i] : 0.0;
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, int64_t nc64, const int32_t *tri, int64_t nbf,
+                               const int32_t *bface, const double *period)
+{
+    if (!s || !xy || !tri || nv < 3 || nc64 < 1 || nc64 > (1 << 30) || nbf < 0 || (nbf > 0 && !bface))
+        return fail(s, CSWDG_EINVAL, "bad mesh arguments");
+    free_device(s);
+    HostMesh H;
+    if (int st = build_host_mesh(s->k, s->bc.kind, nv, xy, nc64, tri, nbf, bface, period, H))
+        return fail(s, (cswdg_status)st, "%s", H.msg.c_str());
+    const int nc = H.nc;
+    s->nc = nc;
+    s->ldc = H.ldc;
+    s->perm = H.perm;
+    s->iperm = H.iperm;
+    s->vtx_user = H.vtx_user;
+    s->rmin = H.rmin;
+    s->nbfaces = (int)H.bfs.size();
+    const int ld = s->ldc;
+    const double rmin = H.rmin;
+    std::vector<double> &geo = H.geo, &scv = H.scv, &arv = H.arv, &vtx = H.vtx, &nvtx = H.nvtx;
+    std::vector<int32_t> &nbr = H.nbr;
+    std::vector<uint8_t> &nbfv = H.nbfv;
+    std::vector<BFace> &bfs = H.bfs;
+    // ---- device buffers ----
+    const size_t rs = s->fp32 ? 4 : 8;
+    const size_t nstate = (size_t)s->nv * s->np * ld;
+    cudaError_t e = cudaSuccess;
+    auto A_ = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A_(cudaMalloc(&s->U, nstate * rs));
+    A_(cudaMalloc(&s->A, nstate * rs));
+    A_(cudaMalloc(&s->B, nstate * rs));
+    A_(cudaMalloc(&s->geo, (size_t)G_COUNT * ld * rs));
+    A_(dalloc(&s->nbr, (size_t)3 * ld));
+    A_(dalloc(&s->nbf, (size_t)ld));
+    A_(dalloc(&s->bf, bfs.size()));
+    A_(dalloc(&s->bcd, 1));
+    A_(dalloc(&s->dperm, (size_t)ld));
+    A_(dalloc(&s->sc, (size_t)ld));
+    A_(dalloc(&s->area, (size_t)ld));
+    A_(dalloc(&s->flags, (size_t)ld));
+    A_(dalloc(&s->flags_user, (size_t)ld));
+    A_(dalloc(&s->flist, (size_t)ld));
+    A_(cudaMalloc(&s->lim_out, (size_t)nc * s->nv * (s->np - 1) * rs));
+    A_(dalloc(&s->ctl, 1));
+    A_(dalloc(&s->dev_user, std::max((size_t)nc * s->nv * s->np, (size_t)nc * 7 * s->nv)));
+    A_(dalloc(&s->cons_part, (size_t)s->nv * ((nc + 255) / 256)));
+    A_(dalloc(&s->cons_out, 4));
+    if (e != cudaSuccess) { free_device(s); return fail(s, CSWDG_ENOMEM, "device allocation: %s", cudaGetErrorString(e)); }
+    cudaStream_t st = s->stream;
+    if (s->fp32) {
+        std::vector<float> g32(geo.begin(), geo.end());
+        CK(cudaMemcpyAsync(s->geo, g32.data(), g32.size() * 4, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        CK(cudaMemcpyAsync(s->geo, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemcpyAsync(s->nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->nbf, nbfv.data(), nbfv.size(), cudaMemcpyHostToDevice, st));
+    if (!bfs.empty()) CK(cudaMemcpyAsync(s->bf, bfs.data(), bfs.size() * sizeof(BFace), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->bcd, &s->bc, sizeof(BcTab), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->dperm, s->perm.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->sc, scv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->area, arv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(s->U, 0, nstate * rs, st));
+    CK(cudaMemsetAsync(s->A, 0, nstate * rs, st));
+    CK(cudaMemsetAsync(s->B, 0, nstate * rs, st));
+    CK(cudaMemsetAsync(s->flags, 0, ld, st));
+    Ctl h{};
+    h.rmin = rmin;
+    h.cfl = s->cfg.cfl;
+    h.active = 1;
+    CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    // ---- per-cell CSWENO operators (set-up kernel, FP64) ----
+    if (s->cfg.limiter != CSWDG_LIMITER_OFF) {
+        const int osz = (s->k == 1) ? Ops<1>::SIZE : Ops<2>::SIZE;
+        double *dops = nullptr, *dvtx = nullptr, *dnvtx = nullptr;
+        e = cudaSuccess;
+        A_(cudaMalloc((void **)&dops, (size_t)nc * osz * 8));
+        A_(cudaMalloc((void **)&dvtx, vtx.size() * 8));
+        A_(cudaMalloc((void **)&dnvtx, nvtx.size() * 8));
+        if (e != cudaSuccess) {
+            cudaFree(dops); cudaFree(dvtx); cudaFree(dnvtx);
+            free_device(s);
+            return fail(s, CSWDG_ENOMEM, "device allocation (stencil operators): %s", cudaGetErrorString(e));
+        }
+        CK(cudaMemcpyAsync(dvtx, vtx.data(), vtx.size() * 8, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dnvtx, nvtx.data(), nvtx.size() * 8, cudaMemcpyHostToDevice, st));
+        // the set-up kernel keeps its QR and Cholesky work arrays on the thread stack
+        size_t stack = 0;
+        CK(cudaDeviceGetLimit(&stack, cudaLimitStackSize));
+        if (stack < 16384) CK(cudaDeviceSetLimit(cudaLimitStackSize, 16384));
+        launch_setup_ops(s->k, nc, ld, dvtx, dnvtx, s->nbr, s->nbf, dops, &s->ctl->err, st);
+        CK(cudaGetLastError());
+        if (s->fp32) {
+            CK(cudaMalloc(&s->ops, (size_t)nc * osz * 4));
+            launch_ops_to_float((size_t)nc * osz, dops, (float *)s->ops, st);
+            CK(cudaGetLastError());
+            CK(cudaStreamSynchronize(st));
+            cudaFree(dops);
+        } else {
+            s->ops = dops;
+        }
+        CK(cudaStreamSynchronize(st));
+        cudaFree(dvtx);
+        cudaFree(dnvtx);
+        Ctl hc;
+        if (cswdg_status r = read_ctl(s, &hc)) return r;
+        if (hc.err & ERR_LSQ) { free_device(s); return fail(s, CSWDG_ELSQ, "rank-deficient stencil least squares"); }
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    s->lim_grid = std::max(1, std::min((nc + 127) / 128, nsm * 8));
+    s->mesh_ready = true;
+    return CSWDG_OK;
+}
+
+int32_t cswdg_num_ic_points(const cswdg_solver *s)
+{
+    if (!s) return 0;
+    return (s->k == 1) ? Deg<1>::QV : Deg<2>::QV;
+}
+
+cswdg_status cswdg_ic_points(cswdg_solver *s, double *xy_host)
+{
+    if (!s || !s->mesh_ready || !xy_host) return fail(s, CSWDG_EINVAL, "ic_points: no mesh or null output");
+    TriRule R;
+    if (s->k == 1) volume_rule<1>(R);
+    else volume_rule<2>(R);
+    for (int c = 0; c < s->nc; ++c) {
+        const double *v = &s->vtx_user[6 * (size_t)c];
+        for (int q = 0; q < R.n; ++q) {
+            xy_host[2 * ((size_t)c * R.n + q)] = R.b[q][0] * v[0] + R.b[q][1] * v[2] + R.b[q][2] * v[4];
+            xy_host[2 * ((size_t)c * R.n + q) + 1] = R.b[q][0] * v[1] + R.b[q][1] * v[3] + R.b[q][2] * v[5];
+        }
+    }
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_project_ic(cswdg_solver *s, const double *values, int32_t apply_limiter)
+{
+    if (!s || !s->mesh_ready || !values) return fail(s, CSWDG_EINVAL, "project_ic: no mesh or null input");
+    const int Q = cswdg_num_ic_points(s);
+    // values are in user cell order: gather into internal order on the host side of the copy
+    std::vector<double> vals((size_t)s->nc * Q * s->nv);
+    for (int i = 0; i < s->nc; ++i)
+        memcpy(&vals[(size_t)i * Q * s->nv], &values[(size_t)s->perm[i] * Q * s->nv], sizeof(double) * Q * s->nv);
+    CK(cudaMemcpyAsync(s->dev_user, vals.data(), vals.size() * 8, cudaMemcpyHostToDevice, s->stream));
+    if (s->fp32) launch_project<float>(s->k, s->nc, s->ldc, s->nv, s->dev_user, (float *)s->U, s->stream);
+    else launch_project<double>(s->k, s->nc, s->ldc, s->nv, s->dev_user, (double *)s->U, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    if (apply_limiter && s->cfg.limiter != CSWDG_LIMITER_OFF) {
+        Ctl h;
+        if (cswdg_status r = read_ctl(s, &h)) return r;
+        Ctl w = h;
+        w.dt = 0.0;
+        w.active = 1;
+        if (cswdg_status r = write_ctl(s, &w)) return r;
+        if (cswdg_status r = limiter_pass(s, s->U, 0.0, s->stream, nullptr, apply_limiter == 2)) return r;
+        Ctl after;
+        if (cswdg_status r = read_ctl(s, &after)) return r;
+        h.nflag = after.nflag;
+        h.err = after.err;
+        if (cswdg_status r = write_ctl(s, &h)) return r;
+        if (cswdg_status r = check_err(s, &h)) return r;
+    }
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *t_out)
+{
+    if (!s || !s->mesh_ready || nsteps < 0) return fail(s, CSWDG_EINVAL, "step: no mesh or negative nsteps");
+    const int use_cfl = !(dt > 0.0);
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    h.t_next = h.t_next;  // the step starts from t_next (= current time)
+    h.dt_fixed = dt;
+    h.cfl = s->cfg.cfl;
+    h.t_end = t_end;
+    h.lam_bits = 0ull;
+    if (cswdg_status r = write_ctl(s, &h)) return r;
+    if (cswdg_status r = get_graph(s, use_cfl)) return r;
+    for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(s->graph[use_cfl], s->stream));
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    h.t = h.t_next;
+    if (t_out) *t_out = h.t_next;
+    return check_err(s, &h);
+}
+
+cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *ms_host, int64_t *launches_host)
+{
+    if (!s || !s->mesh_ready || nsteps < 0 || !ms_host) return fail(s, CSWDG_EINVAL, "profile_step");
+    const int use_cfl = !(dt > 0.0);
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    h.dt_fixed = dt;
+    h.cfl = s->cfg.cfl;
+    h.t_end = t_end;
+    h.lam_bits = 0ull;
+    if (cswdg_status r = write_ctl(s, &h)) return r;
+    for (int i = 0; i < KC_COUNT; ++i) ms_host[i] = 0.0;
+    int64_t nl = 0;
+    for (int64_t it = 0; it < nsteps; ++it) {
+        Prof prof;
+        mark(&prof, -1, s->stream);
+        if (cswdg_status r = record_step(s, use_cfl, s->stream, &prof)) return r;
+        CK(cudaStreamSynchronize(s->stream));
+        for (size_t i = 1; i < prof.ev.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, prof.ev[i - 1].second, prof.ev[i].second);
+            ms_host[prof.ev[i].first] += ms;
+        }
+        nl += (int64_t)prof.ev.size() - 1 + (use_cfl ? 1 : 0);
+        for (auto &e : prof.ev) cudaEventDestroy(e.second);
+    }
+    if (launches_host) *launches_host = nl;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    return check_err(s, &h);
+}
+
+int32_t cswdg_launches_per_step(const cswdg_solver *s, int32_t use_cfl)
+{
+    if (!s) return 0;
+    const int lim = (s->cfg.limiter != CSWDG_LIMITER_OFF) ? 3 : 0;
+    return (use_cfl ? 2 : 1) + 3 * (1 + lim);
+}
+
+cswdg_status cswdg_get_time(cswdg_solver *s, double *t)
+{
+    if (!s || !s->mesh_ready || !t) return fail(s, CSWDG_EINVAL, "get_time");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    *t = h.t_next;
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_set_time(cswdg_solver *s, double t)
+{
+    if (!s || !s->mesh_ready) return fail(s, CSWDG_EINVAL, "set_time");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    h.t = h.t_next = t;
+    return write_ctl(s, &h);
+}
+
+cswdg_status cswdg_read_modes(cswdg_solver *s, double *modes)
+{
+    if (!s || !s->mesh_ready || !modes) return fail(s, CSWDG_EINVAL, "read_modes");
+    return download_modes(s, s->U, modes);
+}
+
+cswdg_status cswdg_write_modes(cswdg_solver *s, const double *modes)
+{
+    if (!s || !s->mesh_ready || !modes) return fail(s, CSWDG_EINVAL, "write_modes");
+    if (cswdg_status r = upload_modes(s, modes, s->U)) return r;
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_read_flags(cswdg_solver *s, uint8_t *flags)
+{
+    if (!s || !s->mesh_ready || !flags) return fail(s, CSWDG_EINVAL, "read_flags");
+    launch_flags_to_user(s->nc, s->dperm, s->flags, s->flags_user, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(flags, s->flags_user, s->nc, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_num_flagged(cswdg_solver *s, int64_t *n)
+{
+    if (!s || !s->mesh_ready || !n) return fail(s, CSWDG_EINVAL, "num_flagged");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    *n = h.nflag;
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_conservation(cswdg_solver *s, double *sums)
+{
+    if (!s || !s->mesh_ready || !sums) return fail(s, CSWDG_EINVAL, "conservation");
+    if (s->fp32) launch_conservation<float>(s->nc, s->ldc, s->nv, s->np, s->area, (const float *)s->U, s->cons_part, s->cons_out, s->stream);
+    else launch_conservation<double>(s->nc, s->ldc, s->nv, s->np, s->area, (const double *)s->U, s->cons_part, s->cons_out, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(sums, s->cons_out, s->nv * 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_eval_rhs(cswdg_solver *s, double t, const double *modes_in, double *rhs)
+{
+    if (!s || !s->mesh_ready || !modes_in || !rhs) return fail(s, CSWDG_EINVAL, "eval_rhs");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.t = t;
+    w.dt = 1.0;
+    w.active = 1;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    if (cswdg_status r = stage(s, nullptr, s->U, s->A, 0.0, 0.0, 1.0, 0.0, s->stream)) return r;
+    if (cswdg_status r = download_modes(s, s->A, rhs)) return r;
+    return write_ctl(s, &h);
+}
+
+cswdg_status cswdg_limit(cswdg_solver *s, double t, const double *modes_in, double *modes_out, uint8_t *flags)
+{
+    if (!s || !s->mesh_ready || !modes_in) return fail(s, CSWDG_EINVAL, "limit");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.t = t;
+    w.dt = 0.0;
+    w.active = 1;
+    w.err = 0;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    if (s->cfg.limiter == CSWDG_LIMITER_OFF) CK(cudaMemsetAsync(s->flags, 0, s->ldc, s->stream));
+    if (cswdg_status r = limiter_pass(s, s->U, 0.0, s->stream)) return r;
+    if (modes_out)
+        if (cswdg_status r = download_modes(s, s->U, modes_out)) return r;
+    if (flags)
+        if (cswdg_status r = cswdg_read_flags(s, flags)) return r;
+    Ctl after;
+    if (cswdg_status r = read_ctl(s, &after)) return r;
+    h.nflag = after.nflag;
+    h.err = after.err;
+    if (cswdg_status r = write_ctl(s, &h)) return r;
+    return check_err(s, &h);
+}
+
+cswdg_status cswdg_cfl_dt(cswdg_solver *s, double *dt)
+{
+    if (!s || !s->mesh_ready || !dt) return fail(s, CSWDG_EINVAL, "cfl_dt");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.lam_bits = 0ull;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (s->fp32) launch_cfl<float>(s->eq, mesh_dev<float>(s), s->np, (const float *)s->U, s->ctl, s->stream);
+    else launch_cfl<double>(s->eq, mesh_dev<double>(s), s->np, (const double *)s->U, s->ctl, s->stream);
+    CK(cudaGetLastError());
+    Ctl after;
+    if (cswdg_status r = read_ctl(s, &after)) return r;
+    double lam;
+    memcpy(&lam, &after.lam_bits, 8);
+    *dt = (lam > 0.0) ? s->cfg.cfl * s->rmin / lam : 0.0;
+    return write_ctl(s, &h);
+}
+
+cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un, const void *uprev, void *out, double a, double b, double dt, double t_rhs)
+{
+    if (!s || !s->mesh_ready || !uprev || !out || (a != 0.0 && !un)) return fail(s, CSWDG_EINVAL, "stage_dev");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.t = t_rhs;
+    w.dt = dt;
+    w.active = 1;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (cswdg_status r = stage(s, a != 0.0 ? un : nullptr, uprev, out, a, b, b, 0.0, s->stream)) return r;
+    CK(cudaStreamSynchronize(s->stream));
+    return write_ctl(s, &h);
+}
+
+cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out, int32_t *n)
+{
+    if (!s || !s->mesh_ready || cell < 0 || cell >= s->nc || !n) return fail(s, CSWDG_EINVAL, "stencil_operator");
+    const int osz = (s->k == 1) ? Ops<1>::SIZE : Ops<2>::SIZE;
+    *n = (s->cfg.limiter == CSWDG_LIMITER_OFF) ? 0 : osz;
+    if (!out || *n == 0) return CSWDG_OK;
+    const size_t off = (size_t)s->iperm[cell] * osz;
+    if (s->fp32) {
+        std::vector<float> tmp(osz);
+        CK(cudaMemcpy(tmp.data(), (const float *)s->ops + off, osz * 4, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < osz; ++i) out[i] = tmp[i];
+    } else {
+        CK(cudaMemcpy(out, (const double *)s->ops + off, osz * 8, cudaMemcpyDeviceToHost));
+    }
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_internal_layout(cswdg_solver *s, int64_t *ldc, int32_t *perm)
+{
+    if (!s || !s->mesh_ready) return fail(s, CSWDG_EINVAL, "internal_layout");
+    if (ldc) *ldc = s->ldc;
+    if (perm)
+        for (int c = 0; c < s->nc; ++c) perm[c] = s->iperm[c];
+    return CSWDG_OK;
+}
+
+}  // extern "C"

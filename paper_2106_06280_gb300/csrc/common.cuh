@@ -1,0 +1,140 @@
+// common.cuh -- shared definitions of the CUDA RKDG + CSWENO library:
+// problem constants, the orthonormal triangle basis (Sec. 2, Eq. triangleBasis),
+// constant-memory quadrature/basis tables and the kernel argument blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define CSW_MAXTAG 16
+#define CSW_MAXPAR 16
+
+namespace csw {
+
+enum { BURGERS = 0, EULER = 1 };
+enum { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_TRANSMISSIVE = 2, BC_WALL = 3, BC_SHOCKLINE = 4 };
+enum { ERR_NONPHYS = 1, ERR_LSQ = 2 };
+
+template <int K> struct Deg {
+    static constexpr int NP = (K + 1) * (K + 2) / 2;  // modes
+    static constexpr int QV = (K == 1) ? 3 : 7;       // volume rule points (degree 2 / 5)
+    static constexpr int QF = (K == 1) ? 2 : 4;       // Gauss-Legendre points per face (degree 3 / 7)
+    static constexpr int QS = NP;                     // reconstruction (SCP-role) points
+    static constexpr int NM = (K == 1) ? 5 : 9;       // non-constant monomials of the top stencil polynomial
+    static constexpr int NSLOT = (K == 1) ? 3 : 4;    // WENO polynomials p_1..p_NSLOT
+    static constexpr int NSUB = 7;                    // subcells per neighbour: 3 thirds + 4 halves
+    static constexpr int NROW = (K == 1) ? 9 : 15;    // rows of the top least-squares problem
+};
+template <int EQ> struct Eqn { static constexpr int NV = (EQ == BURGERS) ? 1 : 4; };
+
+// ---------------------------------------------------------------------------
+// Orthonormal Dubiner basis psi_m(r, s), Sec. 2 Eq. triangleBasis, with
+// L2-normalised Jacobi polynomials; modes ordered i outer, j inner.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline double jac_unnorm(int n, double a, double b, double x)
+{
+    double p0 = 1.0;
+    if (n == 0) return p0;
+    double p1 = 0.5 * ((a + b + 2.0) * x + (a - b));
+    for (int m = 2; m <= n; ++m) {
+        const double c = 2.0 * m + a + b;
+        const double p2 = ((c - 1.0) * (c * (c - 2.0) * x + a * a - b * b) * p1 -
+                           2.0 * (m + a - 1.0) * (m + b - 1.0) * c * p0) /
+                          (2.0 * m * (m + a + b) * (c - 2.0));
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// 1 / sqrt(2^{alpha+1} / (2n + alpha + 1)), the L2 normalisation of P_n^{(alpha,0)}
+__host__ __device__ inline double jac_inv_norm(int n, int alpha)
+{
+    return sqrt((2.0 * n + alpha + 1.0) / (double)(2 << alpha));
+}
+
+__host__ __device__ inline void mode_pair(int k, int m, int &i, int &j)
+{
+    int idx = 0;
+    i = 0;
+    j = 0;
+    for (int a = 0; a <= k; ++a)
+        for (int b = 0; b <= k - a; ++b) {
+            if (idx == m) { i = a; j = b; }
+            ++idx;
+        }
+}
+
+// value and (r,s) gradient of psi_m
+__host__ __device__ inline void dubiner(int k, int m, double r, double s, double &v, double &dr, double &ds)
+{
+    int i, j;
+    mode_pair(k, m, i, j);
+    const double omb = 1.0 - s;
+    const double a = (omb > 0.0) ? 2.0 * (1.0 + r) / omb - 1.0 : -1.0;
+    const double ni = jac_inv_norm(i, 0), nj = jac_inv_norm(j, 2 * i + 1);
+    const double Pa = jac_unnorm(i, 0.0, 0.0, a) * ni;
+    const double dPa = (i > 0) ? 0.5 * (i + 1.0) * jac_unnorm(i - 1, 1.0, 1.0, a) * ni : 0.0;
+    const double Qb = jac_unnorm(j, 2.0 * i + 1.0, 0.0, s) * nj;
+    const double dQb = (j > 0) ? 0.5 * (j + 2.0 * i + 2.0) * jac_unnorm(j - 1, 2.0 * i + 2.0, 1.0, s) * nj : 0.0;
+    double wi = 1.0, wim1 = 0.0;
+    for (int t = 0; t < i; ++t) { wim1 = wi; wi *= omb; }
+    const double sq2 = 1.4142135623730951;
+    v = sq2 * Pa * Qb * wi;
+    dr = sq2 * dPa * Qb * 2.0 * wim1;
+    ds = sq2 * (dPa * (1.0 + a) * Qb * wim1 + Pa * dQb * wi - i * Pa * Qb * wim1);
+}
+
+// ---------------------------------------------------------------------------
+// Constant-memory tables (filled once per process from the host rules).
+// ---------------------------------------------------------------------------
+template <typename R, int K> struct Tab {
+    R vphi[Deg<K>::QV][Deg<K>::NP];   // psi_m at the volume points
+    R vdr[Deg<K>::QV][Deg<K>::NP];    // d psi_m / dr
+    R vds[Deg<K>::QV][Deg<K>::NP];    // d psi_m / ds
+    R vw[Deg<K>::QV];                 // volume weights (sum 1)
+    R fphi[3][Deg<K>::QF][Deg<K>::NP];// psi_m at the Gauss points of local face f
+    R fw[Deg<K>::QF];                 // face weights (sum 1)
+    R ft[Deg<K>::QF];                 // Gauss points as edge parameters in [0,1]
+};
+
+// per-boundary-face data (double: used in boundary decisions)
+struct BFace {
+    double ax, ay, bx, by;  // endpoints, interior on the left of a->b
+    double nx, ny;          // outward unit normal
+    int32_t tag, pad;
+};
+
+struct BcTab {
+    int32_t kind[CSW_MAXTAG];
+    double par[CSW_MAXTAG][CSW_MAXPAR];
+};
+
+// step control words in device memory
+struct Ctl {
+    double t;        // time at the start of the current step
+    double dt;       // step of the current step (0: inactive)
+    unsigned long long lam_bits;  // max wave speed (bits of a non-negative double)
+    double t_next;   // t + dt
+    double cfl, t_end, dt_fixed, rmin;
+    int32_t err;     // sticky error bits
+    int32_t nflag;   // flagged-cell count of the last pass
+    int32_t active;  // 1: kernels run; 0: step beyond t_end, kernels return
+    int32_t pad;
+};
+
+// geometry array indices (REAL, SoA with leading dimension ldc)
+enum { G_RX = 0, G_RY, G_SX, G_SY, G_N0X, G_N0Y, G_N0L, G_N1X, G_N1Y, G_N1L, G_N2X, G_N2Y, G_N2L, G_KAPPA, G_COUNT };
+
+template <typename R> struct MeshDev {
+    int nc;
+    int ldc;
+    const R *geo;           // [G_COUNT][ldc]
+    const int32_t *nbr;     // [3][ldc]: >= 0 neighbour, < 0: -(bface+1)
+    const uint8_t *nbf;     // [ldc]: neighbour local faces, 2 bits per face
+    const BFace *bf;        // boundary faces
+    const BcTab *bc;
+    double gamma;
+};
+
+}  // namespace csw

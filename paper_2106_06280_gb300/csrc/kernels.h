@@ -1,0 +1,53 @@
+// kernels.h -- host-side launchers of the CUDA kernels (one translation unit
+// per group of kernels; this header is the only coupling between them).
+#pragma once
+#include "common.cuh"
+
+namespace csw {
+
+// per-cell CSWENO operator block (REAL values, one block per cell)
+template <int K> struct Ops {
+    static constexpr int NP = Deg<K>::NP, NM = Deg<K>::NM;
+    static constexpr int NSUBK = (K == 1) ? 3 : 7;      // thirds (+ halves for P2)
+    static constexpr int W = 0;                          // [3][NSUBK][NP] subcell-mean weights
+    static constexpr int A2 = W + 3 * NSUBK * NP;        // [2][3]  pseudo-inverse, linear fit on T2
+    static constexpr int A3 = A2 + 6;                    // [5][9]  quadratic fit on T3
+    static constexpr int A4 = A3 + 45;                   // [9][15] cubic fit on T4 (P2)
+    static constexpr int LH = A4 + ((K == 2) ? 135 : 0); // packed lower Cholesky factor of the beta form
+    static constexpr int MI = LH + NM * (NM + 1) / 2;    // [3][2][2] beta_1 gradient maps
+    static constexpr int PHI = MI + 12;                  // [NP-1][NM] projection to modes 1..NP-1
+    static constexpr int HB = PHI + (NP - 1) * NM;       // mean side length of the cell
+    static constexpr int SIZE = (HB + 2) & ~1;
+};
+
+cudaError_t operator_upload_tables();
+cudaError_t limiter_upload_tables();
+
+template <typename R>
+void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
+                  const Ctl *ctl, cudaStream_t st);
+template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st);
+void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st);
+template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);
+template <typename R>
+void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st);
+template <typename R>
+void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, double *user, cudaStream_t st);
+void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st);
+template <typename R>
+void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st);
+
+// limiter
+void launch_setup_ops(int k, int nc, int ld, const double *vtx, const double *nvtx, const int32_t *nbr, const uint8_t *nbf,
+                      double *ops, int32_t *err, cudaStream_t st);
+void launch_ops_to_float(size_t n, const double *src, float *dst, cudaStream_t st);
+template <typename R>
+void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
+                   int32_t *flist, cudaStream_t st);
+template <typename R>
+void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl,
+                  double tfac, R *lim_out, int grid, cudaStream_t st);
+template <typename R>
+void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st);
+
+}  // namespace csw

@@ -1,0 +1,762 @@
+// limiter.cu -- KXRCF troubled-cell detection (Sec. 3.1, Eq.
+// troubledCellIndicator) and the compact subcell WENO reconstruction of the
+// flagged cells (Sec. 3.2), plus the set-up kernel that builds each cell's
+// stencil operators once per mesh.
+//
+// Per flagged cell the reconstruction needs only immediate neighbours: their
+// modes are turned into subcell means by fixed weights, the means into the
+// least-squares stencil polynomials by fixed pseudo-inverses, the
+// polynomials into smoothness indicators by a fixed quadratic form, and the
+// weighted combination into modes by a fixed projection.  All of these depend
+// on geometry only, so the set-up kernel computes them in FP64 (Householder
+// QR, Cholesky) and stores one operator block per cell (Ops<K>); the
+// per-stage kernel applies them.  Smoothness-indicator sums, nonlinear weights
+// and the KXRCF threshold test are always evaluated in FP64.
+#include "kernels.h"
+#include "physics.cuh"
+#include "rules.cuh"
+#include "tables.cuh"
+
+namespace csw {
+
+__constant__ Tab<float, 1> lT_f1;
+__constant__ Tab<float, 2> lT_f2;
+__constant__ Tab<double, 1> lT_d1;
+__constant__ Tab<double, 2> lT_d2;
+
+template <typename R, int K> __device__ __forceinline__ const Tab<R, K> &ltab();
+template <> __device__ __forceinline__ const Tab<float, 1> &ltab<float, 1>() { return lT_f1; }
+template <> __device__ __forceinline__ const Tab<float, 2> &ltab<float, 2>() { return lT_f2; }
+template <> __device__ __forceinline__ const Tab<double, 1> &ltab<double, 1>() { return lT_d1; }
+template <> __device__ __forceinline__ const Tab<double, 2> &ltab<double, 2>() { return lT_d2; }
+
+cudaError_t limiter_upload_tables()
+{
+    static Tab<float, 1> f1;
+    static Tab<float, 2> f2;
+    static Tab<double, 1> d1;
+    static Tab<double, 2> d2;
+    make_tab(f1); make_tab(f2); make_tab(d1); make_tab(d2);
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(lT_f1, &f1, sizeof(f1))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(lT_f2, &f2, sizeof(f2))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(lT_d1, &d1, sizeof(d1))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(lT_d2, &d2, sizeof(d2));
+}
+
+// ===========================================================================
+// Set-up: per-cell operators (FP64, one thread per cell)
+// ===========================================================================
+
+struct P2d { double x, y; };
+
+__host__ __device__ inline P2d tri_pt(const P2d *T, const double *b)
+{
+    return P2d{b[0] * T[0].x + b[1] * T[1].x + b[2] * T[2].x, b[0] * T[0].y + b[1] * T[1].y + b[2] * T[2].y};
+}
+
+// physical point -> reference (r, s) of triangle V (vertex order as stored)
+__host__ __device__ inline void to_ref(const P2d *V, P2d p, double &r, double &s)
+{
+    const double a11 = V[1].x - V[0].x, a12 = V[2].x - V[0].x, a21 = V[1].y - V[0].y, a22 = V[2].y - V[0].y;
+    const double det = a11 * a22 - a12 * a21, dx = p.x - V[0].x, dy = p.y - V[0].y;
+    r = 2.0 * (a22 * dx - a12 * dy) / det - 1.0;
+    s = 2.0 * (-a21 * dx + a11 * dy) / det - 1.0;
+}
+
+__host__ __device__ inline P2d mirror(P2d a, P2d b, P2d p)
+{
+    const double ex = b.x - a.x, ey = b.y - a.y;
+    const double t = ((p.x - a.x) * ex + (p.y - a.y) * ey) / (ex * ex + ey * ey);
+    return P2d{2.0 * (a.x + t * ex) - p.x, 2.0 * (a.y + t * ey) - p.y};
+}
+
+// foot of the perpendicular from c on edge a->b; midpoint unless strictly inside [0.05, 0.95]
+__host__ __device__ inline P2d perp_foot(P2d c, P2d a, P2d b)
+{
+    const double ex = b.x - a.x, ey = b.y - a.y;
+    double t = ((c.x - a.x) * ex + (c.y - a.y) * ey) / (ex * ex + ey * ey);
+    if (!(t >= 0.05 && t <= 0.95)) t = 0.5;
+    return P2d{a.x + t * ex, a.y + t * ey};
+}
+
+// degree-graded monomials xi^a eta^b without the constant: index j -> (a, b)
+__host__ __device__ inline void mono_ab(int j, int &a, int &b)
+{
+    int idx = 0;
+    a = b = 0;
+    for (int d = 1; d <= 4; ++d)
+        for (int e = 0; e <= d; ++e) {
+            if (idx == j) { a = d - e; b = e; }
+            ++idx;
+        }
+}
+
+__host__ __device__ inline double powi(double x, int n)
+{
+    double r = 1.0;
+    for (int i = 0; i < n; ++i) r *= x;
+    return r;
+}
+
+// d^{p+q}/dxi^p deta^q of xi^a eta^b at (xi, eta)
+__host__ __device__ inline double dmono(int a, int b, int p, int q, double xi, double eta)
+{
+    if (p > a || q > b) return 0.0;
+    double c = 1.0;
+    for (int i = 0; i < p; ++i) c *= (a - i);
+    for (int i = 0; i < q; ++i) c *= (b - i);
+    return c * powi(xi, a - p) * powi(eta, b - q);
+}
+
+// Moore-Penrose pseudo-inverse of a full-column-rank m x n matrix (row-major)
+// through Householder QR: P = R^{-1} Q^T, written P[j*m + i].  Returns 0 or -1.
+// Kept out of line: inlined into the set-up kernel, the optimised sm_103a build
+// returned a wrong 9 x 5 pseudo-inverse (the -G build and an out-of-line call
+// agree with the host and with the oracle).
+__host__ __device__ __noinline__ int pinv_qr(int m, int n, double *A, double *P)
+{
+    double diag[16], beta[16];
+    double rmax = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < m; ++i) nrm += A[i * n + j] * A[i * n + j];
+        nrm = sqrt(nrm);
+        if (nrm == 0.0) return -1;
+        const double alpha = (A[j * n + j] > 0.0) ? -nrm : nrm;
+        A[j * n + j] -= alpha;  // v stored in column j below/at the diagonal
+        double vv = 0.0;
+        for (int i = j; i < m; ++i) vv += A[i * n + j] * A[i * n + j];
+        beta[j] = (vv > 0.0) ? 2.0 / vv : 0.0;
+        for (int col = j + 1; col < n; ++col) {
+            double s = 0.0;
+            for (int i = j; i < m; ++i) s += A[i * n + j] * A[i * n + col];
+            s *= beta[j];
+            for (int i = j; i < m; ++i) A[i * n + col] -= s * A[i * n + j];
+        }
+        diag[j] = alpha;
+        if (fabs(alpha) > rmax) rmax = fabs(alpha);
+    }
+    for (int j = 0; j < n; ++j)
+        if (fabs(diag[j]) < 1e-13 * rmax) return -1;
+    for (int e = 0; e < m; ++e) {
+        double y[16];
+        for (int i = 0; i < m; ++i) y[i] = (i == e) ? 1.0 : 0.0;
+        for (int j = 0; j < n; ++j) {  // y <- Q^T y
+            double s = 0.0;
+            for (int i = j; i < m; ++i) s += A[i * n + j] * y[i];
+            s *= beta[j];
+            for (int i = j; i < m; ++i) y[i] -= s * A[i * n + j];
+        }
+        for (int j = n - 1; j >= 0; --j) {  // R x = y
+            double s = y[j];
+            for (int col = j + 1; col < n; ++col) s -= A[j * n + col] * P[col * m + e];
+            P[j * m + e] = s / diag[j];
+        }
+    }
+    return 0;
+}
+
+// operator block of cell c; returns non-zero on a rank-deficient fit
+template <int K>
+__host__ __device__ int setup_cell(int c, int ld, const double *vtx, const double *nvtx, const int32_t *nbr, const uint8_t *nbf,
+                                   double *op)
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NM = Deg<K>::NM, NSUBK = O::NSUBK;
+    TriRule r2, r4, rs;
+    rule_deg2(r2);
+    rule_deg4(r4);
+    recon_rule<K>(rs);
+
+    P2d P[3];
+    for (int i = 0; i < 3; ++i) P[i] = P2d{vtx[(size_t)c * 6 + 2 * i], vtx[(size_t)c * 6 + 2 * i + 1]};
+    const double area = 0.5 * ((P[1].x - P[0].x) * (P[2].y - P[0].y) - (P[2].x - P[0].x) * (P[1].y - P[0].y));
+    const double h0 = sqrt(area);
+    const P2d x0{(P[0].x + P[1].x + P[2].x) / 3.0, (P[0].y + P[1].y + P[2].y) / 3.0};
+    const double hbar = (hypot(P[1].x - P[0].x, P[1].y - P[0].y) + hypot(P[2].x - P[1].x, P[2].y - P[1].y) +
+                         hypot(P[0].x - P[2].x, P[0].y - P[2].y)) / 3.0;
+
+    // monomial means over Delta_0 (degree-4 rule, exact up to degree 4)
+    double m0[NM];
+    for (int j = 0; j < NM; ++j) {
+        int a, b;
+        mono_ab(j, a, b);
+        double s = 0.0;
+        for (int q = 0; q < r4.n; ++q) {
+            const P2d p = tri_pt(P, r4.b[q]);
+            s += r4.w[q] * powi((p.x - x0.x) / h0, a) * powi((p.y - x0.y) / h0, b);
+        }
+        m0[j] = s;
+    }
+
+    // least-squares rows: stencil cells in the order [i1 of slots 0..2, then per slot its other cells]
+    double rowT[3][NSUBK][NM];  // mean_S(m_j) - m0_j for every subcell S
+    for (int f = 0; f < 3; ++f) {
+        const int code = nbr[f * ld + c];
+        P2d X[3], NVt[3];
+        int nfl = 0;
+        if (code >= 0) {
+            for (int i = 0; i < 3; ++i) NVt[i] = P2d{nvtx[((size_t)c * 3 + f) * 6 + 2 * i], nvtx[((size_t)c * 3 + f) * 6 + 2 * i + 1]};
+            nfl = (nbf[c] >> (2 * f)) & 3;
+            for (int i = 0; i < 3; ++i) X[i] = NVt[(nfl + i) % 3];
+        } else {
+            X[0] = P[(f + 1) % 3];
+            X[1] = P[f];
+            X[2] = mirror(P[f], P[(f + 1) % 3], P[(f + 2) % 3]);
+        }
+        const P2d cx{(X[0].x + X[1].x + X[2].x) / 3.0, (X[0].y + X[1].y + X[2].y) / 3.0};
+        P2d S[7][3];
+        S[0][0] = cx; S[0][1] = X[0]; S[0][2] = X[1];
+        S[1][0] = cx; S[1][1] = X[1]; S[1][2] = X[2];
+        S[2][0] = cx; S[2][1] = X[2]; S[2][2] = X[0];
+        if (K == 2) {
+            const P2d f2 = perp_foot(cx, X[1], X[2]), f3 = perp_foot(cx, X[2], X[0]);
+            S[3][0] = cx; S[3][1] = X[1]; S[3][2] = f2;
+            S[4][0] = cx; S[4][1] = f2;   S[4][2] = X[2];
+            S[5][0] = cx; S[5][1] = f3;   S[5][2] = X[0];
+            S[6][0] = cx; S[6][1] = X[2]; S[6][2] = f3;
+        }
+        for (int i = 0; i < NSUBK; ++i) {
+            // subcell-mean weights: mean over S of psi_m of the neighbour (or, for a
+            // ghost, of this cell at the mirrored point)
+            for (int m = 0; m < NP; ++m) {
+                double s = 0.0;
+                for (int q = 0; q < r2.n; ++q) {
+                    P2d p = tri_pt(S[i], r2.b[q]);
+                    double rr, ss, v, dr, ds;
+                    if (code >= 0) to_ref(NVt, p, rr, ss);
+                    else {
+                        p = mirror(P[f], P[(f + 1) % 3], p);
+                        to_ref(P, p, rr, ss);
+                    }
+                    dubiner(K, m, rr, ss, v, dr, ds);
+                    s += r2.w[q] * v;
+                }
+                op[O::W + (f * NSUBK + i) * NP + m] = s;
+            }
+            for (int j = 0; j < NM; ++j) {
+                int a, b;
+                mono_ab(j, a, b);
+                double s = 0.0;
+                for (int q = 0; q < r4.n; ++q) {
+                    const P2d p = tri_pt(S[i], r4.b[q]);
+                    s += r4.w[q] * powi((p.x - x0.x) / h0, a) * powi((p.y - x0.y) / h0, b);
+                }
+                rowT[f][i][j] = s - m0[j];
+            }
+        }
+        // beta_1 map: centroids of the thirds in the (xi, eta) frame
+        double cxs[3], cys[3];
+        for (int i = 0; i < 3; ++i) {
+            cxs[i] = ((S[i][0].x + S[i][1].x + S[i][2].x) / 3.0 - x0.x) / h0;
+            cys[i] = ((S[i][0].y + S[i][1].y + S[i][2].y) / 3.0 - x0.y) / h0;
+        }
+        const double a11 = cxs[1] - cxs[0], a12 = cys[1] - cys[0], a21 = cxs[2] - cxs[0], a22 = cys[2] - cys[0];
+        const double det = a11 * a22 - a12 * a21;
+        op[O::MI + 4 * f + 0] = a22 / det;
+        op[O::MI + 4 * f + 1] = -a12 / det;
+        op[O::MI + 4 * f + 2] = -a21 / det;
+        op[O::MI + 4 * f + 3] = a11 / det;
+    }
+
+    // pseudo-inverses
+    double A[15 * 9], Pm[9 * 15];
+    int bad = 0;
+    for (int s = 0; s < 3; ++s)
+        for (int j = 0; j < 2; ++j) A[s * 2 + j] = rowT[s][0][j];
+    if (pinv_qr(3, 2, A, Pm)) bad = 1;
+    for (int i = 0; i < 6; ++i) op[O::A2 + i] = Pm[i];
+    {
+        int r = 0;
+        for (int s = 0; s < 3; ++s, ++r)
+            for (int j = 0; j < 5; ++j) A[r * 5 + j] = rowT[s][0][j];
+        for (int s = 0; s < 3; ++s)
+            for (int i = 1; i < 3; ++i, ++r)
+                for (int j = 0; j < 5; ++j) A[r * 5 + j] = rowT[s][i][j];
+        if (pinv_qr(9, 5, A, Pm)) bad = 1;
+        for (int i = 0; i < 45; ++i) op[O::A3 + i] = Pm[i];
+    }
+    if (K == 2) {
+        int r = 0;
+        for (int s = 0; s < 3; ++s, ++r)
+            for (int j = 0; j < 9; ++j) A[r * 9 + j] = rowT[s][0][j];
+        for (int s = 0; s < 3; ++s)
+            for (int i = 3; i < NSUBK; ++i, ++r)
+                for (int j = 0; j < 9; ++j) A[r * 9 + j] = rowT[s][i][j];
+        if (pinv_qr(15, 9, A, Pm)) bad = 1;
+        for (int i = 0; i < 135; ++i) op[O::A4 + i] = Pm[i];
+    }
+
+    // smoothness-indicator form H_jk = sum_{1<=|alpha|<=deg} int_{Delta_0 in xi} D^a m_j D^a m_k,
+    // Delta_0 has unit area in the xi frame; integrand degree <= 4
+    constexpr int DEG = (K == 1) ? 2 : 3;
+    double H[NM][NM];
+    for (int j = 0; j < NM; ++j)
+        for (int k = 0; k < NM; ++k) H[j][k] = 0.0;
+    for (int q = 0; q < r4.n; ++q) {
+        const P2d p = tri_pt(P, r4.b[q]);
+        const double xi = (p.x - x0.x) / h0, eta = (p.y - x0.y) / h0;
+        for (int s = 1; s <= DEG; ++s)
+            for (int qq = 0; qq <= s; ++qq) {
+                const int pp = s - qq;
+                double d[NM];
+                for (int j = 0; j < NM; ++j) {
+                    int a, b;
+                    mono_ab(j, a, b);
+                    d[j] = dmono(a, b, pp, qq, xi, eta);
+                }
+                for (int j = 0; j < NM; ++j)
+                    for (int k = 0; k < NM; ++k) H[j][k] += r4.w[q] * d[j] * d[k];
+            }
+    }
+    // Cholesky H = L L^T, packed rows of L
+    double L[NM][NM];
+    for (int i = 0; i < NM; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = H[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) { bad = 1; s = 1e-300; }
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    for (int i = 0, p = 0; i < NM; ++i)
+        for (int j = 0; j <= i; ++j, ++p) op[O::LH + p] = L[i][j];
+
+    // projection of sum_j c_j (m_j - m0_j) onto modes 1..NP-1 through the
+    // reconstruction points: Phi_ij = 2 sum_q w_q (m_j(xi_q) - m0_j) psi_i(r_q)
+    for (int i = 1; i < NP; ++i)
+        for (int j = 0; j < NM; ++j) {
+            int a, b;
+            mono_ab(j, a, b);
+            double s = 0.0;
+            for (int q = 0; q < rs.n; ++q) {
+                const P2d p = tri_pt(P, rs.b[q]);
+                double rr, ss, v, dr, ds;
+                bary_to_rs(rs.b[q], rr, ss);
+                dubiner(K, i, rr, ss, v, dr, ds);
+                s += rs.w[q] * (powi((p.x - x0.x) / h0, a) * powi((p.y - x0.y) / h0, b) - m0[j]) * v;
+            }
+            op[O::PHI + (i - 1) * NM + j] = 2.0 * s;
+        }
+    op[O::HB] = hbar;
+    return bad;
+}
+
+template <int K>
+__global__ void k_setup_ops(int nc, int ld, const double *__restrict__ vtx, const double *__restrict__ nvtx,
+                            const int32_t *__restrict__ nbr, const uint8_t *__restrict__ nbf, double *__restrict__ ops,
+                            int32_t *err)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    if (setup_cell<K>(c, ld, vtx, nvtx, nbr, nbf, ops + (size_t)c * Ops<K>::SIZE)) atomicOr(err, ERR_LSQ);
+}
+
+void launch_setup_ops(int k, int nc, int ld, const double *vtx, const double *nvtx, const int32_t *nbr, const uint8_t *nbf,
+                      double *ops, int32_t *err, cudaStream_t st)
+{
+    const int blk = 64, grd = (nc + blk - 1) / blk;
+    if (k == 1) k_setup_ops<1><<<grd, blk, 0, st>>>(nc, ld, vtx, nvtx, nbr, nbf, ops, err);
+    else k_setup_ops<2><<<grd, blk, 0, st>>>(nc, ld, vtx, nvtx, nbr, nbf, ops, err);
+}
+
+__global__ void k_to_float(size_t n, const double *__restrict__ s, float *__restrict__ d)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) d[i] = (float)s[i];
+}
+void launch_ops_to_float(size_t n, const double *src, float *dst, cudaStream_t st) { k_to_float<<<1024, 256, 0, st>>>(n, src, dst); }
+
+// ===========================================================================
+// KXRCF detection + compaction of the flagged cells
+// ===========================================================================
+
+// ghost value of the indicator variable (variable 0) across a boundary face
+template <int EQ, typename R>
+__device__ __forceinline__ R ghost0(const BFace &bf, const BcTab *bc, double tp, double t, R Uin0)
+{
+    const int kind = bc->kind[bf.tag];
+    const double *P = bc->par[bf.tag];
+    if (kind == BC_DIRICHLET) return (R)P[0];
+    if (kind == BC_SHOCKLINE) {
+        constexpr int NV = Eqn<EQ>::NV;
+        const double x = bf.ax + tp * (bf.bx - bf.ax), y = bf.ay + tp * (bf.by - bf.ay);
+        return (R)((x < P[0] + y * P[1] + P[2] * t) ? P[3] : P[3 + NV]);
+    }
+    return Uin0;  // transmissive, and the wall keeps the density
+}
+
+template <int EQ, int K, typename R>
+__global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, int all,
+                                                uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
+{
+    constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF;
+    if (!ctl->active) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ld = M.ldc;
+    const double is2 = 0.70710678118654752440;
+    int flag = 0;
+    if (c < M.nc) {
+        const Tab<R, K> &T = ltab<R, K>();
+        const double tl = ctl->t + tfac * ctl->dt;
+        R a[NP];
+        for (int m = 0; m < NP; ++m) a[m] = u[m * ld + c];
+        double vx, vy;
+        if (EQ == EULER) {
+            const double r = (double)a[0] * is2, mx = (double)u[(1 * NP) * ld + c] * is2, my = (double)u[(2 * NP) * ld + c] * is2;
+            const double E = (double)u[(3 * NP) * ld + c] * is2;
+            const double p = (M.gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / r);
+            if (!(r > 0.0 && p > 0.0)) atomicOr(&ctl->err, ERR_NONPHYS);
+            vx = mx / r;
+            vy = my / r;
+        } else {
+            vx = vy = (double)a[0] * is2;
+            if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+        }
+        if (all) {
+            flag = 1;
+        } else {
+            double num = 0.0, lsum = 0.0;
+            const unsigned nbfc = M.nbf[c];
+            for (int f = 0; f < 3; ++f) {
+                const double nx = (double)M.geo[(G_N0X + 3 * f) * ld + c], ny = (double)M.geo[(G_N0Y + 3 * f) * ld + c];
+                // inflow test v.n < 0 without contraction (exact zero for v = (u, u) on n = (a, -a))
+                const double vn = (EQ == BURGERS) ? vx * __dadd_rn(nx, ny) : __dadd_rn(__dmul_rn(vx, nx), __dmul_rn(vy, ny));
+                if (!(vn < 0.0)) continue;
+                const double nl = (double)M.geo[(G_N0L + 3 * f) * ld + c];
+                const int code = M.nbr[f * ld + c];
+                const int nf = (nbfc >> (2 * f)) & 3;
+                R w[NP];
+                BFace bf;
+                if (code >= 0) {
+                    for (int m = 0; m < NP; ++m) w[m] = u[m * ld + code];
+                } else {
+                    bf = M.bf[-code - 1];
+                }
+                R J = R(0);
+                for (int g = 0; g < QF; ++g) {
+                    R ui = R(0), uo = R(0);
+                    for (int m = 0; m < NP; ++m) ui += a[m] * T.fphi[f][g][m];
+                    if (code >= 0) {
+                        for (int m = 0; m < NP; ++m) uo += w[m] * T.fphi[nf][QF - 1 - g][m];
+                    } else {
+                        uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], tl, ui);
+                    }
+                    J += T.fw[g] * (ui - uo);
+                }
+                num += nl * (double)J;
+                lsum += nl;
+            }
+            double nrm2 = 0.0;
+            for (int m = 0; m < NP; ++m) nrm2 += (double)a[m] * (double)a[m];
+            const double kap = (double)M.geo[G_KAPPA * ld + c];
+            double Rj;
+            if (lsum == 0.0) Rj = 0.0;
+            else if (nrm2 == 0.0) Rj = (fabs(num) > 0.0) ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
+            else Rj = fabs(num) / (lsum * kap * sqrt(nrm2));
+            flag = Rj > ck;
+        }
+        flags[c] = (uint8_t)flag;
+    }
+    // warp-aggregated compaction
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
+    }
+}
+
+template <typename R>
+void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
+                   int32_t *flist, cudaStream_t st)
+{
+    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    if (eq == BURGERS && k == 1) k_detect<BURGERS, 1, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
+    else if (eq == BURGERS && k == 2) k_detect<BURGERS, 2, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
+    else if (eq == EULER && k == 1) k_detect<EULER, 1, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
+    else k_detect<EULER, 2, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
+}
+template void launch_detect<float>(int, int, const MeshDev<float> &, const float *, Ctl *, double, double, int, uint8_t *, int32_t *,
+                                   cudaStream_t);
+template void launch_detect<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
+                                    int32_t *, cudaStream_t);
+
+// ===========================================================================
+// CSWENO reconstruction of one scalar field (Sec. 3.2 Steps 1-5 / Steps 1-4)
+// t[f][i]: subcell means of slot f (thirds 0..2, halves 3..6), w0: cell mean.
+// ===========================================================================
+template <int K, typename R>
+__host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, const R (&t)[3][Ops<K>::NSUBK], R w0, R (&md)[Deg<K>::NP - 1])
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NM = Deg<K>::NM;
+    const double eps = 1e-10;
+    // Step 1: least-squares stencil polynomials (mean on Delta_0 built in)
+    R q2[2], q3[5], q4[9];
+    {
+        R b[3];
+        for (int s = 0; s < 3; ++s) b[s] = t[s][0] - w0;
+        for (int j = 0; j < 2; ++j) {
+            R acc = R(0);
+            for (int s = 0; s < 3; ++s) acc += op[O::A2 + j * 3 + s] * b[s];
+            q2[j] = acc;
+        }
+    }
+    {
+        R b[9];
+        b[0] = t[0][0] - w0; b[1] = t[1][0] - w0; b[2] = t[2][0] - w0;
+        for (int s = 0; s < 3; ++s) { b[3 + 2 * s] = t[s][1] - w0; b[4 + 2 * s] = t[s][2] - w0; }
+        for (int j = 0; j < 5; ++j) {
+            R acc = R(0);
+            for (int s = 0; s < 9; ++s) acc += op[O::A3 + j * 9 + s] * b[s];
+            q3[j] = acc;
+        }
+    }
+    if (K == 2) {
+        R b[15];
+        b[0] = t[0][0] - w0; b[1] = t[1][0] - w0; b[2] = t[2][0] - w0;
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i < 4; ++i) b[3 + 4 * s + i] = t[s][(3 + i) % Ops<K>::NSUBK] - w0;
+        for (int j = 0; j < 9; ++j) {
+            R acc = R(0);
+            for (int s = 0; s < 15; ++s) acc += op[O::A4 + j * 15 + s] * b[s];
+            q4[j] = acc;
+        }
+    }
+    // Step 2: linear weights (1/h)^{l-1}, normalised, and hierarchical polynomials
+    const double ih = 1.0 / (double)op[O::HB];
+    const double s2 = 1.0 + ih, s3 = 1.0 + ih + ih * ih, s5 = 1.0 + ih + ih * ih + ih * ih * ih;
+    const double g22 = ih / s2, g23 = ih / s3, g33 = ih * ih / s3;
+    const double g5[4] = {1.0 / s5, ih / s5, ih * ih / s5, ih * ih * ih / s5};
+    const double g3[3] = {1.0 / s3, g23, g33};
+    R p2[NM], p3[NM], p4[NM];
+    for (int j = 0; j < NM; ++j) { p2[j] = R(0); p3[j] = R(0); p4[j] = R(0); }
+    for (int j = 0; j < 2; ++j) p2[j] = q2[j] / (R)g22;
+    for (int j = 0; j < 5; ++j) p3[j] = (q3[j] - (R)g23 * p2[j]) / (R)g33;
+    if (K == 2)
+        for (int j = 0; j < 9; ++j) p4[j] = (q4[j] - (R)g5[1] * p2[j] - (R)g5[2] * p3[j]) / (R)g5[3];
+    // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2 (sums in FP64)
+    double beta[4];
+    {
+        const R *L = op + O::LH;
+        const int nn[3] = {2, 5, 9};
+        const R *pp[3] = {p2, p3, p4};
+        for (int l = 0; l < Deg<K>::NSLOT - 1; ++l) {
+            double acc = 0.0;
+            for (int j = 0; j < nn[l]; ++j) {
+                R y = R(0);
+                for (int i = j; i < nn[l]; ++i) y += L[i * (i + 1) / 2 + j] * pp[l][i];
+                acc += (double)y * (double)y;
+            }
+            beta[l + 1] = acc;
+        }
+    }
+    // beta_1: magnified from the three linear fits through the thirds' centroids (Eqs. sigmaEqn, smoothnessIndicatorT1)
+    {
+        double al[3], bl[3], b1[3];
+        for (int f = 0; f < 3; ++f) {
+            const double r1 = (double)t[f][1] - (double)t[f][0], r2 = (double)t[f][2] - (double)t[f][0];
+            al[f] = (double)op[O::MI + 4 * f + 0] * r1 + (double)op[O::MI + 4 * f + 1] * r2;
+            bl[f] = (double)op[O::MI + 4 * f + 2] * r1 + (double)op[O::MI + 4 * f + 3] * r2;
+            b1[f] = al[f] * al[f] + bl[f] * bl[f];
+        }
+        const double d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
+        const double D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
+        double sg[3], ss = 0.0;
+        for (int f = 0; f < 3; ++f) { sg[f] = (1.0 / 3.0) * (1.0 + D * D / (b1[f] + eps)); ss += sg[f]; }
+        double ab = 0.0, bb = 0.0;
+        for (int f = 0; f < 3; ++f) { ab += sg[f] / ss * al[f]; bb += sg[f] / ss * bl[f]; }
+        beta[0] = ab * ab + bb * bb;
+    }
+    // Step 4: tau and nonlinear weights (FP64)
+    double om[4];
+    if (K == 1) {
+        const double e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
+        const double tau = (e1 * e1 + e2 * e2) / 4.0;
+        double sw = 0.0;
+        for (int l = 0; l < 3; ++l) { om[l] = g3[l] * (1.0 + tau / (eps + beta[l])); sw += om[l]; }
+        for (int l = 0; l < 3; ++l) om[l] /= sw;
+        om[3] = 0.0;
+    } else {
+        const double e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
+        const double tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
+        double sw = 0.0;
+        for (int l = 0; l < 4; ++l) { om[l] = g5[l] * (1.0 + tau / (eps + beta[l])); sw += om[l]; }
+        for (int l = 0; l < 4; ++l) om[l] /= sw;
+    }
+    // Step 5: combined polynomial (p_1 is the constant cell mean) projected onto modes 1..NP-1
+    R cm[NM];
+    for (int j = 0; j < NM; ++j) cm[j] = (R)om[1] * p2[j] + (R)om[2] * p3[j] + (R)om[3] * p4[j];
+    for (int i = 0; i < NP - 1; ++i) {
+        R acc = R(0);
+        for (int j = 0; j < NM; ++j) acc += op[O::PHI + i * NM + j] * cm[j];
+        md[i] = acc;
+    }
+}
+
+// left/right eigenvectors of the Euler flux Jacobian along the unit direction (nx, ny)
+template <typename R>
+__host__ __device__ __forceinline__ void euler_eig(const R *U, R gam, R nx, R ny, R (&Rm)[4][4], R (&Lm)[4][4])
+{
+    const R rho = U[0], u = U[1] / rho, v = U[2] / rho;
+    const R q2 = u * u + v * v;
+    const R p = (gam - R(1)) * (U[3] - R(0.5) * rho * q2);
+    const R c2 = gam * p / rho, c = rsqrt_(c2), H = (U[3] + p) / rho;
+    const R un = u * nx + v * ny, ut = -u * ny + v * nx, b = gam - R(1);
+    // columns: acoustic (-), entropy, shear, acoustic (+)
+    Rm[0][0] = R(1);          Rm[0][1] = R(1);          Rm[0][2] = R(0); Rm[0][3] = R(1);
+    Rm[1][0] = u - c * nx;    Rm[1][1] = u;             Rm[1][2] = -ny;  Rm[1][3] = u + c * nx;
+    Rm[2][0] = v - c * ny;    Rm[2][1] = v;             Rm[2][2] = nx;   Rm[2][3] = v + c * ny;
+    Rm[3][0] = H - c * un;    Rm[3][1] = R(0.5) * q2;   Rm[3][2] = ut;   Rm[3][3] = H + c * un;
+    const R i2c2 = R(1) / (R(2) * c2);
+    Lm[0][0] = (R(0.5) * b * q2 + c * un) * i2c2; Lm[0][1] = -(b * u + c * nx) * i2c2; Lm[0][2] = -(b * v + c * ny) * i2c2; Lm[0][3] = b * i2c2;
+    Lm[1][0] = R(1) - b * q2 * i2c2;              Lm[1][1] = R(2) * b * u * i2c2;     Lm[1][2] = R(2) * b * v * i2c2;     Lm[1][3] = -R(2) * b * i2c2;
+    Lm[2][0] = -ut;                               Lm[2][1] = -ny;                     Lm[2][2] = nx;                      Lm[2][3] = R(0);
+    Lm[3][0] = (R(0.5) * b * q2 - c * un) * i2c2; Lm[3][1] = -(b * u - c * nx) * i2c2; Lm[3][2] = -(b * v - c * ny) * i2c2; Lm[3][3] = b * i2c2;
+}
+
+// reconstructed modes 1..NP-1 of every variable of flagged cell c (Sec. 3.2),
+// from the unlimited state u, at limiter time tl
+template <int EQ, int K, typename R>
+__host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R *u, const R *op, int c, double tl,
+                                                    R (&res)[Eqn<EQ>::NV][Deg<K>::NP - 1])
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NV = Eqn<EQ>::NV, NSUBK = O::NSUBK;
+    const int ld = M.ldc;
+    const R gam = (R)M.gamma;
+    R u0[NV][NP];
+    for (int v = 0; v < NV; ++v)
+        for (int m = 0; m < NP; ++m) u0[v][m] = u[(v * NP + m) * ld + c];
+    R mean[NV][3][NSUBK];
+    for (int f = 0; f < 3; ++f) {
+        const int code = M.nbr[f * ld + c];
+        R w[NV][NP];
+        bool constant = false;
+        if (code >= 0) {
+            for (int v = 0; v < NV; ++v)
+                for (int m = 0; m < NP; ++m) w[v][m] = u[(v * NP + m) * ld + code];
+        } else {
+            const BFace bf = M.bf[-code - 1];
+            const int kind = M.bc->kind[bf.tag];
+            if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
+                // constant ghost (shock line: decided at the face midpoint)
+                R S[NV], dummy[NV];
+                for (int v = 0; v < NV; ++v) dummy[v] = R(0);
+                ghost<EQ, R>(bf, M.bc, 0.5, tl, dummy, S);
+                for (int v = 0; v < NV; ++v)
+                    for (int i = 0; i < NSUBK; ++i) mean[v][f][i] = S[v];
+                constant = true;
+            } else {
+                for (int v = 0; v < NV; ++v)
+                    for (int m = 0; m < NP; ++m) w[v][m] = u0[v][m];
+                if (kind == BC_WALL && EQ == EULER) {
+                    const R nx = (R)bf.nx, ny = (R)bf.ny;
+                    for (int m = 0; m < NP; ++m) {
+                        const R mn = w[1][m] * nx + w[2][m] * ny;
+                        w[1][m] -= R(2) * mn * nx;
+                        w[2][m] -= R(2) * mn * ny;
+                    }
+                }
+            }
+        }
+        if (!constant)
+            for (int i = 0; i < NSUBK; ++i)
+                for (int v = 0; v < NV; ++v) {
+                    R s = R(0);
+                    for (int m = 0; m < NP; ++m) s += op[O::W + (f * NSUBK + i) * NP + m] * w[v][m];
+                    mean[v][f][i] = s;
+                }
+    }
+    R ub[NV];
+    for (int v = 0; v < NV; ++v) ub[v] = u0[v][0] * R(0.70710678118654752440);
+    if (EQ == BURGERS) {
+        R md[NP - 1];
+        weno_field<K, R>(op, mean[0], ub[0], md);
+        for (int i = 0; i < NP - 1; ++i) res[0][i] = md[i];
+    } else {
+        for (int v = 0; v < NV; ++v)
+            for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+        for (int d = 0; d < 2; ++d) {
+            R Rm[4][4], Lm[4][4];
+            euler_eig<R>(ub, gam, d == 0 ? R(1) : R(0), d == 0 ? R(0) : R(1), Rm, Lm);
+            for (int fl = 0; fl < 4; ++fl) {
+                R tc[3][NSUBK];
+                for (int f = 0; f < 3; ++f)
+                    for (int i = 0; i < NSUBK; ++i) {
+                        R s = R(0);
+                        for (int v = 0; v < 4; ++v) s += Lm[fl][v] * mean[v][f][i];
+                        tc[f][i] = s;
+                    }
+                R w0 = R(0);
+                for (int v = 0; v < 4; ++v) w0 += Lm[fl][v] * ub[v];
+                R md[NP - 1];
+                weno_field<K, R>(op, tc, w0, md);
+                for (int v = 0; v < 4; ++v)
+                    for (int i = 0; i < NP - 1; ++i) res[v][i] += R(0.5) * Rm[v][fl] * md[i];
+            }
+        }
+    }
+}
+
+template <int EQ, int K, typename R>
+__global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
+                                               const int32_t *__restrict__ flist, const Ctl *__restrict__ ctl, double tfac,
+                                               R *__restrict__ lim_out)
+{
+    constexpr int NP = Deg<K>::NP, NV = Eqn<EQ>::NV;
+    if (!ctl->active) return;
+    const int n = ctl->nflag;
+    const double tl = ctl->t + tfac * ctl->dt;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int c = flist[idx];
+        R res[NV][NP - 1];
+        limit_cell<EQ, K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
+        for (int v = 0; v < NV; ++v)
+            for (int i = 0; i < NP - 1; ++i) lim_out[((size_t)idx * NV + v) * (NP - 1) + i] = res[v][i];
+    }
+}
+
+template <typename R>
+void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl, double tfac,
+                  R *lim_out, int grid, cudaStream_t st)
+{
+    const int blk = 128;
+    if (eq == BURGERS && k == 1) k_limit<BURGERS, 1, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    else if (eq == BURGERS && k == 2) k_limit<BURGERS, 2, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    else if (eq == EULER && k == 1) k_limit<EULER, 1, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    else k_limit<EULER, 2, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+}
+template void launch_limit<float>(int, int, const MeshDev<float> &, const float *, const float *, const int32_t *, const Ctl *, double,
+                                  float *, int, cudaStream_t);
+template void launch_limit<double>(int, int, const MeshDev<double> &, const double *, const double *, const int32_t *, const Ctl *,
+                                   double, double *, int, cudaStream_t);
+
+template <typename R>
+__global__ void k_scatter(int nv, int np, int ld, const int32_t *__restrict__ flist, const R *__restrict__ lim_out, R *__restrict__ u,
+                          const Ctl *__restrict__ ctl)
+{
+    if (!ctl->active) return;
+    const int n = ctl->nflag;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int c = flist[idx];
+        for (int v = 0; v < nv; ++v)
+            for (int i = 1; i < np; ++i) u[(v * np + i) * ld + c] = lim_out[((size_t)idx * nv + v) * (np - 1) + i - 1];
+    }
+}
+
+template <typename R>
+void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st)
+{
+    k_scatter<R><<<grid, 256, 0, st>>>(nv, np, ld, flist, lim_out, u, ctl);
+}
+template void launch_scatter<float>(int, int, int, const int32_t *, const float *, float *, const Ctl *, int, cudaStream_t);
+template void launch_scatter<double>(int, int, int, const int32_t *, const double *, double *, const Ctl *, int, cudaStream_t);
+
+}  // namespace csw

@@ -1,0 +1,356 @@
+// operator.cu -- the RKDG spatial operator fused with the SSP-RK stage update
+// (Sec. 2, Eq. weakFormScheme2D with quadrature; Sec. 3.2, Eq. timeIntegrate),
+// the CFL reduction, the initial-condition projection, conservation sums and
+// the user-layout <-> internal-layout conversions.
+//
+// Owner-computes: one thread per cell evaluates its volume integral and the
+// three face integrals from its own and its neighbours' traces, so no face
+// buffer, colouring or atomics are needed; the shared-face flux is computed by
+// both cells (the path is bandwidth-bound, the flops are cheap).
+//
+// State in HBM: SoA [var][mode][cell], coefficients of the reference-orthonormal
+// basis (u_tilde = sqrt(2/|K|) u_hat), so that
+//   d u_tilde_i/dt = sum_q W_q grad_r psi_i . (G F(u_q))
+//                   - sum_faces sum_g w_g psi_i(r_g) F*(u-, u+; n_tilde),
+// with G = 2 (dr/dx, dr/dy, ds/dx, ds/dy) and n_tilde = 2 |e| n / |K|.
+#include "kernels.h"
+#include "physics.cuh"
+#include "tables.cuh"
+
+namespace csw {
+
+__constant__ Tab<float, 1> cT_f1;
+__constant__ Tab<float, 2> cT_f2;
+__constant__ Tab<double, 1> cT_d1;
+__constant__ Tab<double, 2> cT_d2;
+
+template <typename R, int K> __device__ __forceinline__ const Tab<R, K> &tab();
+template <> __device__ __forceinline__ const Tab<float, 1> &tab<float, 1>() { return cT_f1; }
+template <> __device__ __forceinline__ const Tab<float, 2> &tab<float, 2>() { return cT_f2; }
+template <> __device__ __forceinline__ const Tab<double, 1> &tab<double, 1>() { return cT_d1; }
+template <> __device__ __forceinline__ const Tab<double, 2> &tab<double, 2>() { return cT_d2; }
+
+cudaError_t operator_upload_tables()
+{
+    static Tab<float, 1> f1;
+    static Tab<float, 2> f2;
+    static Tab<double, 1> d1;
+    static Tab<double, 2> d2;
+    make_tab(f1); make_tab(f2); make_tab(d1); make_tab(d2);
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbol(cT_f1, &f1, sizeof(f1))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cT_f2, &f2, sizeof(f2))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(cT_d1, &d1, sizeof(d1))) != cudaSuccess) return e;
+    return cudaMemcpyToSymbol(cT_d2, &d2, sizeof(d2));
+}
+
+// ---------------------------------------------------------------------------
+// Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
+// ---------------------------------------------------------------------------
+template <int EQ, int K, typename R>
+__global__ void __launch_bounds__(128) k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up,
+                                              R *out, R ca, R cb, R cl, double tfac, const Ctl *__restrict__ ctl)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
+    if (!ctl->active) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= M.nc) return;
+    const Tab<R, K> &T = tab<R, K>();
+    const int ld = M.ldc;
+    const R gam = (R)M.gamma;
+    const double dt = ctl->dt;
+    const double trhs = ctl->t + tfac * dt;
+
+    R u[NV][NP], acc[NV][NP];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            u[v][m] = up[(v * NP + m) * ld + c];
+            acc[v][m] = R(0);
+        }
+    const R g0 = M.geo[G_RX * ld + c], g1 = M.geo[G_RY * ld + c], g2 = M.geo[G_SX * ld + c], g3 = M.geo[G_SY * ld + c];
+
+    // volume integral
+#pragma unroll
+    for (int q = 0; q < QV; ++q) {
+        R U[NV], f[NV], g[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R s = R(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) s += u[v][m] * T.vphi[q][m];
+            U[v] = s;
+        }
+        flux_fg<EQ, R>(U, gam, f, g);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const R Fr = T.vw[q] * (g0 * f[v] + g1 * g[v]);
+            const R Fs = T.vw[q] * (g2 * f[v] + g3 * g[v]);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) acc[v][m] += T.vdr[q][m] * Fr + T.vds[q][m] * Fs;
+        }
+    }
+
+    // face integrals
+    const unsigned nbf = M.nbf[c];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c], nl = M.geo[(G_N0L + 3 * f) * ld + c];
+        const int code = M.nbr[f * ld + c];
+        R w[NV][NP];
+        int nf = (nbf >> (2 * f)) & 3;
+        BFace bf;
+        if (code >= 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NP; ++m) w[v][m] = up[(v * NP + m) * ld + code];
+        } else {
+            bf = M.bf[-code - 1];
+        }
+#pragma unroll
+        for (int g = 0; g < QF; ++g) {
+            R Ui[NV], Uo[NV], F[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R s = R(0);
+#pragma unroll
+                for (int m = 0; m < NP; ++m) s += u[v][m] * T.fphi[f][g][m];
+                Ui[v] = s;
+            }
+            if (code >= 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R s = R(0);
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[nf][QF - 1 - g][m];
+                    Uo[v] = s;
+                }
+            } else {
+                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], trhs, Ui, Uo);
+            }
+            llf<EQ, R>(Ui, Uo, nx, ny, nl, gam, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const R wf = T.fw[g] * F[v];
+#pragma unroll
+                for (int m = 0; m < NP; ++m) acc[v][m] -= T.fphi[f][g][m] * wf;
+            }
+        }
+    }
+
+    const R cdt = cl * (R)dt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            R r = cb * u[v][m] + cdt * acc[v][m];
+            if (un) r += ca * un[(v * NP + m) * ld + c];
+            out[(v * NP + m) * ld + c] = r;
+        }
+}
+
+template <typename R>
+void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
+                  const Ctl *ctl, cudaStream_t st)
+{
+    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    if (eq == BURGERS && k == 1) k_stage<BURGERS, 1, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+    else if (eq == BURGERS && k == 2) k_stage<BURGERS, 2, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+    else if (eq == EULER && k == 1) k_stage<EULER, 1, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+    else k_stage<EULER, 2, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+}
+template void launch_stage<float>(int, int, const MeshDev<float> &, const float *, const float *, float *, float, float, float,
+                                  double, const Ctl *, cudaStream_t);
+template void launch_stage<double>(int, int, const MeshDev<double> &, const double *, const double *, double *, double, double,
+                                   double, double, const Ctl *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Time step control.  Max wave speed of the cell means (exact max, order free),
+// then dt = cfl * rmin / lambda_max clipped to t_end (one thread).
+// ---------------------------------------------------------------------------
+template <int EQ, typename R>
+__global__ void __launch_bounds__(256) k_cfl_max(MeshDev<R> M, int np, const R *__restrict__ u, Ctl *ctl)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double lam = 0.0;
+    if (c < M.nc) {
+        const int ld = M.ldc;
+        const double is2 = 0.70710678118654752440;
+        if (EQ == BURGERS) {
+            lam = 1.4142135623730951 * fabs((double)u[c] * is2);
+        } else {
+            const double r = (double)u[(0 * np) * ld + c] * is2, mx = (double)u[(1 * np) * ld + c] * is2;
+            const double my = (double)u[(2 * np) * ld + c] * is2, E = (double)u[(3 * np) * ld + c] * is2;
+            const double uu = mx / r, vv = my / r;
+            const double p = (M.gamma - 1.0) * (E - 0.5 * (mx * uu + my * vv));
+            lam = sqrt(uu * uu + vv * vv) + sqrt(M.gamma * p / r);
+            if (!(lam >= 0.0)) lam = 1.0e300;  // NaN state: force a tiny step, flagged by the positivity check
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    __shared__ double sm[8];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = lam;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = sm[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sm[i]);
+        atomicMax(&ctl->lam_bits, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// begin a step: t <- t_next, choose dt (fixed or CFL), clip to t_end
+__global__ void k_begin_step(Ctl *ctl, int use_cfl)
+{
+    ctl->t = ctl->t_next;
+    double dt = ctl->dt_fixed;
+    if (use_cfl) {
+        const double lam = __longlong_as_double((long long)ctl->lam_bits);
+        dt = (lam > 0.0) ? ctl->cfl * ctl->rmin / lam : 0.0;
+    }
+    const double rem = ctl->t_end - ctl->t;
+    if (dt > rem) dt = rem;
+    if (!(dt > 0.0)) dt = 0.0;
+    ctl->dt = dt;
+    ctl->active = dt > 0.0;
+    ctl->t_next = ctl->t + dt;
+    ctl->lam_bits = 0ull;
+}
+
+template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st)
+{
+    const int blk = 256, grd = (M.nc + blk - 1) / blk;
+    if (eq == BURGERS) k_cfl_max<BURGERS, R><<<grd, blk, 0, st>>>(M, np, u, ctl);
+    else k_cfl_max<EULER, R><<<grd, blk, 0, st>>>(M, np, u, ctl);
+}
+template void launch_cfl<float>(int, const MeshDev<float> &, int, const float *, Ctl *, cudaStream_t);
+template void launch_cfl<double>(int, const MeshDev<double> &, int, const double *, Ctl *, cudaStream_t);
+
+void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st) { k_begin_step<<<1, 1, 0, st>>>(ctl, use_cfl); }
+
+// ---------------------------------------------------------------------------
+// Initial condition: u_tilde_i = 2 sum_q W_q u(x_q) psi_i(r_q) (volume rule).
+// vals: internal order, [cell][q][var] doubles.
+// ---------------------------------------------------------------------------
+template <int K, typename R>
+__global__ void k_project(int nc, int ld, int nv, const double *__restrict__ vals, R *__restrict__ u)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const Tab<double, K> &T = tab<double, K>();
+    for (int v = 0; v < nv; ++v)
+        for (int m = 0; m < NP; ++m) {
+            double s = 0.0;
+            for (int q = 0; q < QV; ++q) s += T.vw[q] * vals[((size_t)c * QV + q) * nv + v] * T.vphi[q][m];
+            u[(v * NP + m) * ld + c] = (R)(2.0 * s);
+        }
+}
+
+template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st)
+{
+    const int blk = 128, grd = (nc + blk - 1) / blk;
+    if (k == 1) k_project<1, R><<<grd, blk, 0, st>>>(nc, ld, nv, vals, u);
+    else k_project<2, R><<<grd, blk, 0, st>>>(nc, ld, nv, vals, u);
+}
+template void launch_project<float>(int, int, int, int, const double *, float *, cudaStream_t);
+template void launch_project<double>(int, int, int, int, const double *, double *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Layout conversions.  user[(uc*nv + v)*np + m] (double, physical basis) <->
+// internal [(v*np + m)*ld + c], scaled by sc[c] = sqrt(2/|K|); perm[c] = user index.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_from_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm, const double *__restrict__ sc,
+                            const double *__restrict__ user, R *__restrict__ u)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const size_t uc = (size_t)perm[c];
+    const double s = sc[c];
+    for (int v = 0; v < nv; ++v)
+        for (int m = 0; m < np; ++m) u[(v * np + m) * ld + c] = (R)(s * user[(uc * nv + v) * np + m]);
+}
+
+template <typename R>
+__global__ void k_to_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm, const double *__restrict__ sc,
+                          const R *__restrict__ u, double *__restrict__ user)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const size_t uc = (size_t)perm[c];
+    const double s = 1.0 / sc[c];
+    for (int v = 0; v < nv; ++v)
+        for (int m = 0; m < np; ++m) user[(uc * nv + v) * np + m] = s * (double)u[(v * np + m) * ld + c];
+}
+
+__global__ void k_flags_to_user(int nc, const int32_t *__restrict__ perm, const uint8_t *__restrict__ fl, uint8_t *__restrict__ out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < nc) out[perm[c]] = fl[c];
+}
+
+template <typename R>
+void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st)
+{
+    k_from_user<R><<<(nc + 255) / 256, 256, 0, st>>>(nc, ld, nv, np, perm, sc, user, u);
+}
+template <typename R>
+void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, double *user, cudaStream_t st)
+{
+    k_to_user<R><<<(nc + 255) / 256, 256, 0, st>>>(nc, ld, nv, np, perm, sc, u, user);
+}
+template void launch_from_user<float>(int, int, int, int, const int32_t *, const double *, const double *, float *, cudaStream_t);
+template void launch_from_user<double>(int, int, int, int, const int32_t *, const double *, const double *, double *, cudaStream_t);
+template void launch_to_user<float>(int, int, int, int, const int32_t *, const double *, const float *, double *, cudaStream_t);
+template void launch_to_user<double>(int, int, int, int, const int32_t *, const double *, const double *, double *, cudaStream_t);
+
+void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st)
+{
+    k_flags_to_user<<<(nc + 255) / 256, 256, 0, st>>>(nc, perm, fl, out);
+}
+
+// ---------------------------------------------------------------------------
+// Conservation sums sum_K |K| mean_K = sum_K |K| u_tilde_0 / sqrt(2):
+// per-block partial sums, then one block adds them in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_cons_partial(int nc, int ld, int nv, int np, const double *__restrict__ area, const R *__restrict__ u,
+                               double *__restrict__ part)
+{
+    __shared__ double sm[256];
+    for (int v = 0; v < nv; ++v) {
+        const int c = blockIdx.x * blockDim.x + threadIdx.x;
+        sm[threadIdx.x] = (c < nc) ? area[c] * (double)u[(v * np) * ld + c] * 0.70710678118654752440 : 0.0;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)v * gridDim.x + blockIdx.x] = sm[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_cons_final(int nblk, int nv, const double *__restrict__ part, double *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    for (int v = 0; v < nv; ++v) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)v * nblk + b];
+        out[v] = s;
+    }
+}
+
+template <typename R>
+void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st)
+{
+    const int nblk = (nc + 255) / 256;
+    k_cons_partial<R><<<nblk, 256, 0, st>>>(nc, ld, nv, np, area, u, part);
+    k_cons_final<<<1, 32, 0, st>>>(nblk, nv, part, out);
+}
+template void launch_conservation<float>(int, int, int, int, const double *, const float *, double *, double *, cudaStream_t);
+template void launch_conservation<double>(int, int, int, int, const double *, const double *, double *, double *, cudaStream_t);
+
+}  // namespace csw

@@ -1,0 +1,236 @@
+"""Thin ctypes binding of ``libcswdg.so`` (include/cswdg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  The functions keep the C names; ``Solver`` wraps one solver handle
+with numpy in/out arrays.  Importing this module loads the library and raises
+if it is missing or cannot be loaded -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcswdg.so")
+
+OK, EINVAL, ECUDA, EMESH, ENONPHYS, ELSQ, ETIMEOUT, ENOMEM = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ECUDA", "EMESH", "ENONPHYS", "ELSQ", "ETIMEOUT", "ENOMEM"]
+BURGERS, EULER = 0, 1
+FP64, FP32_BULK = 0, 1
+LIMITER_OFF, LIMITER_KXRCF, LIMITER_ALL = 0, 1, 2
+
+
+class cswdg_config(C.Structure):
+    _fields_ = [("equation", C.c_int32), ("degree", C.c_int32), ("precision", C.c_int32),
+                ("limiter", C.c_int32), ("c_k", C.c_double), ("cfl", C.c_double),
+                ("gamma", C.c_double), ("stream", C.c_void_p)]
+
+
+class CswdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2106_06280_gb300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+    sig = {
+        "cswdg_create": ([C.POINTER(cswdg_config), C.POINTER(vp)], C.c_int),
+        "cswdg_destroy": ([vp], None),
+        "cswdg_last_error": ([vp], C.c_char_p),
+        "cswdg_set_boundary": ([vp, i32, i32, dp, i32], C.c_int),
+        "cswdg_mesh_upload": ([vp, i64, dp, i64, C.POINTER(i32), i64, C.POINTER(i32), dp], C.c_int),
+        "cswdg_num_ic_points": ([vp], i32),
+        "cswdg_ic_points": ([vp, dp], C.c_int),
+        "cswdg_project_ic": ([vp, dp, i32], C.c_int),
+        "cswdg_step": ([vp, C.c_double, i64, C.c_double, dp], C.c_int),
+        "cswdg_profile_step": ([vp, C.c_double, i64, C.c_double, dp, C.POINTER(i64)], C.c_int),
+        "cswdg_launches_per_step": ([vp, i32], i32),
+        "cswdg_get_time": ([vp, dp], C.c_int),
+        "cswdg_set_time": ([vp, C.c_double], C.c_int),
+        "cswdg_read_modes": ([vp, dp], C.c_int),
+        "cswdg_write_modes": ([vp, dp], C.c_int),
+        "cswdg_read_flags": ([vp, C.POINTER(C.c_uint8)], C.c_int),
+        "cswdg_num_flagged": ([vp, C.POINTER(i64)], C.c_int),
+        "cswdg_conservation": ([vp, dp], C.c_int),
+        "cswdg_eval_rhs": ([vp, C.c_double, dp, dp], C.c_int),
+        "cswdg_limit": ([vp, C.c_double, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
+        "cswdg_cfl_dt": ([vp, dp], C.c_int),
+        "cswdg_stage_dev": ([vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double], C.c_int),
+        "cswdg_internal_layout": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
+        "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+lib = _load()
+EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boundary", "cswdg_mesh_upload",
+            "cswdg_num_ic_points", "cswdg_ic_points", "cswdg_project_ic", "cswdg_step", "cswdg_profile_step",
+            "cswdg_launches_per_step", "cswdg_get_time",
+            "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
+            "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
+            "cswdg_internal_layout", "cswdg_stencil_operator"]
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a, ctype=C.c_double):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Solver:
+    """One solver handle.  equation: BURGERS/EULER, degree 1/2, precision
+    FP64/FP32_BULK, limiter LIMITER_*; stream: a cudaStream_t as int (e.g.
+    torch.cuda.current_stream().cuda_stream) or None."""
+
+    def __init__(self, equation, degree, precision=FP64, limiter=LIMITER_KXRCF, c_k=1.0, cfl=0.1,
+                 gamma=1.4, stream=None):
+        cfg = cswdg_config(equation, degree, precision, limiter, c_k, cfl, gamma, stream)
+        h = C.c_void_p()
+        st = lib.cswdg_create(C.byref(cfg), C.byref(h))
+        if st != OK:
+            raise CswdgError(st, "cswdg_create failed")
+        self.h = h
+        self.nvar = 1 if equation == BURGERS else 4
+        self.np = (degree + 1) * (degree + 2) // 2
+        self.nc = 0
+
+    def _chk(self, st):
+        if st != OK:
+            raise CswdgError(st, lib.cswdg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.cswdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_boundary(self, tag, kind, params=()):
+        p = _d(list(params) + [0.0])
+        self._chk(lib.cswdg_set_boundary(self.h, tag, kind, _p(p), len(params)))
+
+    def mesh_upload(self, xy, tri, bface, period=None):
+        xy = _d(xy)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        bface = np.ascontiguousarray(bface, dtype=np.int32)
+        per = None if period is None else _d(period)
+        self._chk(lib.cswdg_mesh_upload(self.h, xy.shape[0], _p(xy), tri.shape[0], _p(tri, C.c_int32),
+                                        bface.shape[0], _p(bface, C.c_int32), None if per is None else _p(per)))
+        self.nc = tri.shape[0]
+
+    def setup(self, problem):
+        """Boundary table and mesh of a workloads.Problem."""
+        for tag, (kind, par) in problem.boundaries.items():
+            self.set_boundary(tag, kind, par)
+        m = problem.mesh
+        self.mesh_upload(m.xy, m.tri, m.bface, m.period)
+
+    def ic_points(self):
+        q = lib.cswdg_num_ic_points(self.h)
+        xy = np.zeros((self.nc, q, 2))
+        self._chk(lib.cswdg_ic_points(self.h, _p(xy)))
+        return xy
+
+    def project_ic(self, fn, apply_limiter=1):
+        """apply_limiter: 0 none, 1 configured limiter once, 2 every cell once."""
+        xy = self.ic_points()
+        vals = _d(fn(xy[..., 0].ravel(), xy[..., 1].ravel())).reshape(self.nc, -1, self.nvar)
+        vals = _d(vals)
+        self._chk(lib.cswdg_project_ic(self.h, _p(vals), int(apply_limiter)))
+
+    def step(self, dt=0.0, nsteps=1, t_end=1e300):
+        t = np.zeros(1)
+        self._chk(lib.cswdg_step(self.h, dt, nsteps, t_end, _p(t)))
+        return float(t[0])
+
+    def profile_step(self, dt=0.0, nsteps=1, t_end=1e300):
+        ms = np.zeros(5)
+        nl = C.c_int64()
+        self._chk(lib.cswdg_profile_step(self.h, dt, nsteps, t_end, _p(ms), C.byref(nl)))
+        return dict(cfl=ms[0], stage=ms[1], detect=ms[2], limit=ms[3], scatter=ms[4]), int(nl.value)
+
+    def launches_per_step(self, use_cfl=True):
+        return int(lib.cswdg_launches_per_step(self.h, int(use_cfl)))
+
+    def get_time(self):
+        t = np.zeros(1)
+        self._chk(lib.cswdg_get_time(self.h, _p(t)))
+        return float(t[0])
+
+    def set_time(self, t):
+        self._chk(lib.cswdg_set_time(self.h, t))
+
+    def read_modes(self, out=None):
+        if out is None:
+            out = np.zeros((self.nc, self.nvar, self.np))
+        self._chk(lib.cswdg_read_modes(self.h, _p(out)))
+        return out
+
+    def write_modes(self, modes):
+        modes = _d(modes)
+        self._chk(lib.cswdg_write_modes(self.h, _p(modes)))
+
+    def read_flags(self):
+        f = np.zeros(self.nc, dtype=np.uint8)
+        self._chk(lib.cswdg_read_flags(self.h, _p(f, C.c_uint8)))
+        return f
+
+    def num_flagged(self):
+        n = C.c_int64()
+        self._chk(lib.cswdg_num_flagged(self.h, C.byref(n)))
+        return int(n.value)
+
+    def conservation(self):
+        s = np.zeros(self.nvar)
+        self._chk(lib.cswdg_conservation(self.h, _p(s)))
+        return s
+
+    def eval_rhs(self, modes, t=0.0):
+        modes = _d(modes)
+        out = np.zeros_like(modes)
+        self._chk(lib.cswdg_eval_rhs(self.h, t, _p(modes), _p(out)))
+        return out
+
+    def limit(self, modes, t=0.0):
+        modes = _d(modes)
+        out = np.zeros_like(modes)
+        fl = np.zeros(self.nc, dtype=np.uint8)
+        self._chk(lib.cswdg_limit(self.h, t, _p(modes), _p(out), _p(fl, C.c_uint8)))
+        return out, fl
+
+    def cfl_dt(self):
+        d = np.zeros(1)
+        self._chk(lib.cswdg_cfl_dt(self.h, _p(d)))
+        return float(d[0])
+
+    def stage_dev(self, un_ptr, uprev_ptr, out_ptr, a, b, dt, t_rhs):
+        self._chk(lib.cswdg_stage_dev(self.h, un_ptr, uprev_ptr, out_ptr, a, b, dt, t_rhs))
+
+    def stencil_operator(self, cell):
+        n = C.c_int32()
+        self._chk(lib.cswdg_stencil_operator(self.h, cell, None, C.byref(n)))
+        out = np.zeros(max(n.value, 1))
+        self._chk(lib.cswdg_stencil_operator(self.h, cell, _p(out), C.byref(n)))
+        return out[: n.value]
+
+    def internal_layout(self):
+        ld = C.c_int64()
+        perm = np.zeros(self.nc, dtype=np.int32)
+        self._chk(lib.cswdg_internal_layout(self.h, C.byref(ld), _p(perm, C.c_int32)))
+        return int(ld.value), perm
