@@ -218,6 +218,7 @@ def run_ours(args):
     t1 = time.perf_counter()
     e2e_value = float(nc) * NP * NV * 3 * e2e_steps * ws / (t1 - t0)
 
+    launches = s.launches_per_step(True) * args.steps
     # FP64 mode on the same workload (secondary)
     fp64 = None
     if args.fp64_steps > 0:
@@ -254,7 +255,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nc * NV * NP * 8,
                 "d2h_bytes_per_step": nc * NV * NP * 8, "steps": e2e_steps,
                 "path": "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)"},
-        "gpu_launches": s.launches_per_step(True) * args.steps,
+        "gpu_launches": launches,
         "clocks": clk,
         "fp64": fp64,
     }

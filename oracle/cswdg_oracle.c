@@ -1232,6 +1232,35 @@ static int limit_cell(const Oracle *o, const double *u, double t, int c, double 
     }
     for (int v = 0; v < 4; ++v)
         for (int i = 1; i < np; ++i) out[v * np + i] = acc[v][i];
+    /* Reading R-pos (the paper states no positivity treatment): if the
+     * reconstructed polynomial has a non-positive density or pressure at a
+     * volume-rule point or a face Gauss point of the cell, the cell keeps
+     * only its mean. */
+    {
+        Tri tc = cell_tri(o, c, 0, 0);
+        int bad = 0;
+        for (int q = 0; q < o->vol.n + 3 * o->nfq && !bad; ++q) {
+            double x, y, U[4] = {0.0, 0.0, 0.0, 0.0};
+            if (q < o->vol.n) {
+                tri_point(&tc, o->vol.b[q], &x, &y);
+            } else {
+                int f = (q - o->vol.n) / o->nfq, g = (q - o->vol.n) % o->nfq;
+                double ax, ay, bx, by, nx, ny, len;
+                face_geom(o, c, f, &ax, &ay, &bx, &by, &nx, &ny, &len);
+                x = ax + o->fx[g] * (bx - ax);
+                y = ay + o->fx[g] * (by - ay);
+            }
+            for (int m = 0; m < np; ++m) {
+                double pm;
+                psi_phys(o, &tc, m, x, y, &pm, NULL, NULL);
+                for (int v = 0; v < 4; ++v) U[v] += out[v * np + m] * pm;
+            }
+            if (!(U[0] > 0.0 && euler_p(o->gam, U) > 0.0)) bad = 1;
+        }
+        if (bad)
+            for (int v = 0; v < 4; ++v)
+                for (int i = 1; i < np; ++i) out[v * np + i] = 0.0;
+    }
     return status;
 }
 

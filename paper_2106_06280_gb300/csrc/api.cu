@@ -436,7 +436,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    s->lim_grid = std::max(1, std::min((nc + 127) / 128, nsm * 8));
+    s->lim_grid = std::max(1, std::min((nc * (s->eq == CSWDG_EULER ? 8 : 1) + 127) / 128, nsm * 16));
     s->mesh_ready = true;
     return CSWDG_OK;
 }

@@ -404,29 +404,38 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
         const double tl = ctl->t + tfac * ctl->dt;
         R a[NP];
         for (int m = 0; m < NP; ++m) a[m] = u[m * ld + c];
-        double vx, vy;
+        // cell-mean velocity direction: v = (m_x, m_y) / rho with rho > 0 (Euler),
+        // v = (u, u) (Burgers); only its sign against each normal is used
+        R vx, vy;
         if (EQ == EULER) {
-            const double r = (double)a[0] * is2, mx = (double)u[(1 * NP) * ld + c] * is2, my = (double)u[(2 * NP) * ld + c] * is2;
-            const double E = (double)u[(3 * NP) * ld + c] * is2;
-            const double p = (M.gamma - 1.0) * (E - 0.5 * (mx * mx + my * my) / r);
-            if (!(r > 0.0 && p > 0.0)) atomicOr(&ctl->err, ERR_NONPHYS);
-            vx = mx / r;
-            vy = my / r;
+            const R r = a[0], mx = u[(1 * NP) * ld + c], my = u[(2 * NP) * ld + c], E = u[(3 * NP) * ld + c];
+            // positivity of the mean without division: rho > 0 and 2 E rho - |m|^2 > 0, decided in
+            // FP64 (FP32 values are first screened with a relative margin; only close calls are
+            // recomputed in FP64)
+            const R q = R(2) * E * r - (mx * mx + my * my);
+            bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
+            if (!ok && !(q != q)) {
+                const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
+                ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
+            }
+            if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
+            vx = mx;
+            vy = my;
         } else {
-            vx = vy = (double)a[0] * is2;
+            vx = vy = a[0];
             if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
         }
         if (all) {
             flag = 1;
         } else {
-            double num = 0.0, lsum = 0.0;
+            R num = R(0), lsum = R(0);
             const unsigned nbfc = M.nbf[c];
             for (int f = 0; f < 3; ++f) {
-                const double nx = (double)M.geo[(G_N0X + 3 * f) * ld + c], ny = (double)M.geo[(G_N0Y + 3 * f) * ld + c];
-                // inflow test v.n < 0 without contraction (exact zero for v = (u, u) on n = (a, -a))
-                const double vn = (EQ == BURGERS) ? vx * __dadd_rn(nx, ny) : __dadd_rn(__dmul_rn(vx, nx), __dmul_rn(vy, ny));
-                if (!(vn < 0.0)) continue;
-                const double nl = (double)M.geo[(G_N0L + 3 * f) * ld + c];
+                const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c];
+                // inflow test v.n < 0, evaluated without contraction (exact zero for v = (u, u) on n = (a, -a))
+                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
+                if (!(vn < R(0))) continue;
+                const R nl = M.geo[(G_N0L + 3 * f) * ld + c];
                 const int code = M.nbr[f * ld + c];
                 const int nf = (nbfc >> (2 * f)) & 3;
                 R w[NP];
@@ -447,17 +456,16 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
                     }
                     J += T.fw[g] * (ui - uo);
                 }
-                num += nl * (double)J;
+                num += nl * J;
                 lsum += nl;
             }
-            double nrm2 = 0.0;
-            for (int m = 0; m < NP; ++m) nrm2 += (double)a[m] * (double)a[m];
-            const double kap = (double)M.geo[G_KAPPA * ld + c];
-            double Rj;
-            if (lsum == 0.0) Rj = 0.0;
-            else if (nrm2 == 0.0) Rj = (fabs(num) > 0.0) ? __longlong_as_double(0x7ff0000000000000ll) : 0.0;
-            else Rj = fabs(num) / (lsum * kap * sqrt(nrm2));
-            flag = Rj > ck;
+            R nrm2 = R(0);
+            for (int m = 0; m < NP; ++m) nrm2 += a[m] * a[m];
+            const R kap = M.geo[G_KAPPA * ld + c];
+            // R_j = |num| / (lsum kap sqrt(nrm2)) > C_K, compared in FP64 without division or root
+            // (all factors non-negative; no inflow face or a zero jump never flags)
+            const double den = (double)lsum * (double)kap;
+            flag = (lsum > R(0)) && ((double)num * (double)num > ck * ck * den * den * (double)nrm2);
         }
         flags[c] = (uint8_t)flag;
     }
@@ -705,21 +713,145 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
     }
 }
 
+// Euler: a reconstruction with non-positive density or pressure (FP64) at a
+// volume point or a face Gauss point of the cell keeps only the cell mean.
+template <int K, typename R>
+__device__ __forceinline__ void positivity_fallback(const R *mean_modes, R (&res)[4][Deg<K>::NP - 1], double gam)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF;
+    const Tab<R, K> &T = ltab<R, K>();
+    bool bad = false;
+    for (int q = 0; q < QV + 3 * QF && !bad; ++q) {
+        const R *phi = (q < QV) ? T.vphi[q] : T.fphi[(q - QV) / QF][(q - QV) % QF];
+        double U[4];
+        for (int v = 0; v < 4; ++v) {
+            R s = mean_modes[v] * phi[0];
+            for (int m = 1; m < NP; ++m) s += res[v][m - 1] * phi[m];
+            U[v] = (double)s;
+        }
+        const double p = (gam - 1.0) * (U[3] - 0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]);
+        if (!(U[0] > 0.0 && p > 0.0)) bad = true;
+    }
+    if (bad)
+        for (int v = 0; v < 4; ++v)
+            for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+}
+
+// Euler: eight lanes per flagged cell, one per (direction d in {x, y},
+// characteristic field); each lane transforms the neighbours' modes into its
+// field, forms the subcell means, reconstructs (weno_field) and maps back by
+// the right eigenvectors; the eight contributions are summed with shuffles.
+template <int K, typename R>
+__device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const R *__restrict__ u, const R *__restrict__ op, int c,
+                                                      double tl, int lane8, R (&res)[4][Deg<K>::NP - 1])
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NSUBK = O::NSUBK;
+    const int ld = M.ldc;
+    const int d = lane8 >> 2, fl = lane8 & 3;
+    R u0[4][NP];
+    for (int v = 0; v < 4; ++v)
+        for (int m = 0; m < NP; ++m) u0[v][m] = u[(v * NP + m) * ld + c];
+    R ub[4];
+    for (int v = 0; v < 4; ++v) ub[v] = u0[v][0] * R(0.70710678118654752440);
+    R Rm[4][4], Lm[4][4];
+    euler_eig<R>(ub, (R)M.gamma, d == 0 ? R(1) : R(0), d == 0 ? R(0) : R(1), Rm, Lm);
+    R tc[3][NSUBK];
+    for (int f = 0; f < 3; ++f) {
+        const int code = M.nbr[f * ld + c];
+        R wc[NP];  // neighbour modes projected on this lane's characteristic field
+        bool constant = false;
+        if (code >= 0) {
+            for (int m = 0; m < NP; ++m) {
+                R s = R(0);
+                for (int v = 0; v < 4; ++v) s += Lm[fl][v] * u[(v * NP + m) * ld + code];
+                wc[m] = s;
+            }
+        } else {
+            const BFace bf = M.bf[-code - 1];
+            const int kind = M.bc->kind[bf.tag];
+            if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
+                R S[4], dummy[4] = {R(0), R(0), R(0), R(0)};
+                ghost<EULER, R>(bf, M.bc, 0.5, tl, dummy, S);
+                R sc = R(0);
+                for (int v = 0; v < 4; ++v) sc += Lm[fl][v] * S[v];
+                for (int i = 0; i < NSUBK; ++i) tc[f][i] = sc;
+                constant = true;
+            } else {
+                const R nx = (R)bf.nx, ny = (R)bf.ny;
+                for (int m = 0; m < NP; ++m) {
+                    R w1 = u0[1][m], w2 = u0[2][m];
+                    if (kind == BC_WALL) {
+                        const R mn = w1 * nx + w2 * ny;
+                        w1 -= R(2) * mn * nx;
+                        w2 -= R(2) * mn * ny;
+                    }
+                    wc[m] = Lm[fl][0] * u0[0][m] + Lm[fl][1] * w1 + Lm[fl][2] * w2 + Lm[fl][3] * u0[3][m];
+                }
+            }
+        }
+        if (!constant)
+            for (int i = 0; i < NSUBK; ++i) {
+                R s = R(0);
+                for (int m = 0; m < NP; ++m) s += op[O::W + (f * NSUBK + i) * NP + m] * wc[m];
+                tc[f][i] = s;
+            }
+    }
+    R w0 = R(0);
+    for (int v = 0; v < 4; ++v) w0 += Lm[fl][v] * ub[v];
+    R md[NP - 1];
+    weno_field<K, R>(op, tc, w0, md);
+    for (int v = 0; v < 4; ++v)
+        for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0.5) * Rm[v][fl] * md[i];
+}
+
 template <int EQ, int K, typename R>
 __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
                                                const int32_t *__restrict__ flist, const Ctl *__restrict__ ctl, double tfac,
                                                R *__restrict__ lim_out)
 {
     constexpr int NP = Deg<K>::NP, NV = Eqn<EQ>::NV;
+    constexpr int G = (EQ == EULER) ? 8 : 1;  // lanes per flagged cell
     if (!ctl->active) return;
     const int n = ctl->nflag;
     const double tl = ctl->t + tfac * ctl->dt;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const int c = flist[idx];
+    const int warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    // the trip count is uniform across a warp, so the shuffles below see every lane
+    for (int base = warp0; base / G < n; base += stride) {
+        const int idx = (base + lane) / G;
+        const bool active = idx < n;
         R res[NV][NP - 1];
-        limit_cell<EQ, K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
         for (int v = 0; v < NV; ++v)
-            for (int i = 0; i < NP - 1; ++i) lim_out[((size_t)idx * NV + v) * (NP - 1) + i] = res[v][i];
+            for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+        const int c = active ? flist[idx] : 0;
+        if (active) {
+            if (EQ == EULER)
+                limit_cell_euler_lane<K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, lane & 7,
+                                            *reinterpret_cast<R(*)[4][NP - 1]>(&res));
+            else
+                limit_cell<EQ, K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
+        }
+        if (EQ == EULER) {
+            for (int v = 0; v < NV; ++v)
+                for (int i = 0; i < NP - 1; ++i) {
+                    R x = res[v][i];
+                    x += __shfl_xor_sync(0xffffffffu, x, 1);
+                    x += __shfl_xor_sync(0xffffffffu, x, 2);
+                    x += __shfl_xor_sync(0xffffffffu, x, 4);
+                    res[v][i] = x;
+                }
+        }
+        if (active && (lane % G) == 0) {
+            if (EQ == EULER) {
+                R m0[4];
+                for (int v = 0; v < NV; ++v) m0[v] = u[(v * NP) * M.ldc + c];
+                positivity_fallback<K, R>(m0, *reinterpret_cast<R(*)[4][NP - 1]>(&res), M.gamma);
+            }
+            for (int v = 0; v < NV; ++v)
+                for (int i = 0; i < NP - 1; ++i) lim_out[((size_t)idx * NV + v) * (NP - 1) + i] = res[v][i];
+        }
     }
 }
 

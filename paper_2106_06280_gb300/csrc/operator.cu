@@ -48,7 +48,7 @@ cudaError_t operator_upload_tables()
 // Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
 // ---------------------------------------------------------------------------
 template <int EQ, int K, typename R>
-__global__ void __launch_bounds__(128) k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up,
+__global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up,
                                               R *out, R ca, R cb, R cl, double tfac, const Ctl *__restrict__ ctl)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
@@ -120,13 +120,18 @@ __global__ void __launch_bounds__(128) k_stage(MeshDev<R> M, const R *un, const 
                 Ui[v] = s;
             }
             if (code >= 0) {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    R s = R(0);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[nf][QF - 1 - g][m];
-                    Uo[v] = s;
-                }
+                // neighbour trace at the same physical point: its local face nf, reversed order;
+                // one branch per face so that the table entries are compile-time constants
+#define CSW_TRACE(NF)                                                                  \
+    _Pragma("unroll") for (int v = 0; v < NV; ++v) {                                  \
+        R s = R(0);                                                                    \
+        _Pragma("unroll") for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[NF][QF - 1 - g][m]; \
+        Uo[v] = s;                                                                     \
+    }
+                if (nf == 0) { CSW_TRACE(0) }
+                else if (nf == 1) { CSW_TRACE(1) }
+                else { CSW_TRACE(2) }
+#undef CSW_TRACE
             } else {
                 ghost<EQ, R>(bf, M.bc, (double)T.ft[g], trhs, Ui, Uo);
             }
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(128) k_stage(MeshDev<R> M, const R *un, const 
         }
     }
 
-    const R cdt = cl * (R)dt;
+    const R cdt = cl * (R)dt;  // one conversion per thread
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -173,30 +178,32 @@ template void launch_stage<double>(int, int, const MeshDev<double> &, const doub
 template <int EQ, typename R>
 __global__ void __launch_bounds__(256) k_cfl_max(MeshDev<R> M, int np, const R *__restrict__ u, Ctl *ctl)
 {
+    // largest wave speed of the cell means in the state precision (an exact
+    // maximum, independent of the reduction order)
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    double lam = 0.0;
+    R lam = R(0);
     if (c < M.nc) {
         const int ld = M.ldc;
-        const double is2 = 0.70710678118654752440;
+        const R is2 = R(0.70710678118654752440);
         if (EQ == BURGERS) {
-            lam = 1.4142135623730951 * fabs((double)u[c] * is2);
+            lam = R(1.4142135623730951) * rabs(u[c] * is2);
         } else {
-            const double r = (double)u[(0 * np) * ld + c] * is2, mx = (double)u[(1 * np) * ld + c] * is2;
-            const double my = (double)u[(2 * np) * ld + c] * is2, E = (double)u[(3 * np) * ld + c] * is2;
-            const double uu = mx / r, vv = my / r;
-            const double p = (M.gamma - 1.0) * (E - 0.5 * (mx * uu + my * vv));
-            lam = sqrt(uu * uu + vv * vv) + sqrt(M.gamma * p / r);
-            if (!(lam >= 0.0)) lam = 1.0e300;  // NaN state: force a tiny step, flagged by the positivity check
+            const R r = u[(0 * np) * ld + c] * is2, mx = u[(1 * np) * ld + c] * is2;
+            const R my = u[(2 * np) * ld + c] * is2, E = u[(3 * np) * ld + c] * is2;
+            const R uu = mx / r, vv = my / r;
+            const R p = ((R)M.gamma - R(1)) * (E - R(0.5) * (mx * uu + my * vv));
+            lam = rsqrt_(uu * uu + vv * vv) + rsqrt_((R)M.gamma * p / r);
+            if (!(lam >= R(0))) lam = R(1e30);  // NaN state: force a tiny step, flagged by the positivity check
         }
     }
-    for (int o = 16; o > 0; o >>= 1) lam = fmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    __shared__ double sm[8];
+    for (int o = 16; o > 0; o >>= 1) lam = rmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    __shared__ R sm[8];
     if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = lam;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = sm[0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, sm[i]);
-        atomicMax(&ctl->lam_bits, (unsigned long long)__double_as_longlong(m));
+        R m = sm[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = rmax(m, sm[i]);
+        atomicMax(&ctl->lam_bits, (unsigned long long)__double_as_longlong((double)m));
     }
 }
 

@@ -1,0 +1,112 @@
+"""GPU checks on the benchmark-family configurations at full size.
+
+* Burgers P1, 20x20 split squares (800 cells), FP64, KXRCF C_K = 1, to t = 0.1:
+  whole run against the oracle (coefficients 1e-11, flags bit-exact at the end).
+* Burgers P2, 160x160 (51,200 cells): 12 steps against the oracle in FP64
+  (1e-11, flags) and in FP32-bulk mode (L1 error relative to the mean |u|
+  below 2e-6); then the GPU alone to t = 1.0 past shock formation: cell-mean
+  conservation, limited cells present, FP32 vs FP64 L1 difference.
+* Double Mach reflection, Euler P2, 960x240 (460,800 cells): one operator
+  evaluation and one limiter pass on a seeded random state, compared with the
+  oracle on 600 sampled cells (FP64: 1e-11 and identical flags).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_06280_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def l1(a, b, area):
+    return float(np.sum(area * np.abs(a[:, 0, 0] - b[:, 0, 0]) / np.sqrt(area)) / np.sum(area))
+
+
+def test_config1_full_run_fp64(csw, cuda_stream):
+    pb = W.burgers_sine(20, seed=1)
+    o = oracle.Oracle(pb, k=1, limiter=1, ck=1.0)
+    s = csw.Solver(0, 1, csw.FP64, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=cuda_stream)
+    s.setup(pb)
+    u0 = o.project(pb.u0)
+    uo, _, _ = o.limit(u0, 0.0)
+    s.write_modes(uo)
+    s.set_time(0.0)
+    t = 0.0
+    n = 0
+    fl = None
+    while t < 0.1:
+        dt = min(o.cfl_dt(uo, 0.1), 0.1 - t)
+        uo, fl, st = o.step(uo, t, dt)
+        t += dt
+        n += 1
+    tg = s.step(0.0, n + 5, 0.1)  # extra steps beyond t_end do nothing
+    assert abs(tg - 0.1) < 1e-15
+    ug = s.read_modes()
+    assert np.array_equal(s.read_flags(), fl)
+    assert np.abs(ug - uo).max() / np.abs(uo).max() < 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_config2_steps_vs_oracle(csw, cuda_stream, precision):
+    pb = W.burgers_sine(160, seed=2)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    s = csw.Solver(0, 2, precision, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=cuda_stream)
+    s.setup(pb)
+    uo = o.project(pb.u0)
+    uo, _, _ = o.limit(uo, 0.0)
+    s.write_modes(uo)
+    s.set_time(0.0)
+    dt = o.cfl_dt(uo, 0.1)
+    for i in range(12):
+        uo, flo, st = o.step(uo, i * dt, dt)
+    s.step(dt, 12, 1e9)
+    ug = s.read_modes()
+    area = W.cell_areas(pb.mesh)
+    if precision == 0:
+        assert np.abs(ug - uo).max() / np.abs(uo).max() < 1e-11
+        assert np.array_equal(s.read_flags(), flo)
+    else:
+        err = l1(ug, uo, area) / 0.5  # mean |u| is 0.5
+        assert err < 2e-6, err
+
+
+def test_config2_to_t1_fp32_vs_fp64(csw, cuda_stream):
+    pb = W.burgers_sine(160, seed=2)
+    out = {}
+    for prec in (0, 1):
+        s = csw.Solver(0, 2, prec, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=cuda_stream)
+        s.setup(pb)
+        s.project_ic(pb.u0, apply_limiter=1)
+        c0 = s.conservation()[0]
+        t = s.step(0.0, 100000, 1.0)
+        assert t == 1.0
+        assert abs(s.conservation()[0] - c0) < (1e-11 if prec == 0 else 1e-5) * abs(c0)
+        assert s.num_flagged() > 0  # a shock has formed (breaking time 2/pi)
+        out[prec] = s.read_modes()
+        s.close()
+    area = W.cell_areas(pb.mesh)
+    assert l1(out[1], out[0], area) < 1e-4
+
+
+def test_config3_full_size_sampled_fp64(csw, cuda_stream):
+    pb = W.double_mach(960, 240, seed=3)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    u = W.random_modes(pb.mesh, 4, 6, 33, scale=0.02)
+    rng = np.random.default_rng(7)
+    cells = np.sort(rng.choice(pb.mesh.nc, 600, replace=False)).astype(np.int32)
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_OFF, stream=cuda_stream)
+    s.setup(pb)
+    Lg = s.eval_rhs(u, 0.05)
+    Lo = o.rhs_cells(u, cells, 0.05)
+    assert np.abs(Lg[cells] - Lo).max() / np.abs(Lo).max() < 1e-11
+    s.close()
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    ug, fg = s.limit(u, 0.05)
+    fo, _ = o.detect_cells(u, cells, 0.05)
+    assert np.array_equal(fg[cells], fo)
+    flagged = cells[fo.astype(bool)]
+    assert len(flagged) > 10
+    lo, st = o.limit_cells(u, flagged, 0.05)
+    assert np.abs(ug[flagged] - lo).max() / np.abs(lo).max() < 1e-11
