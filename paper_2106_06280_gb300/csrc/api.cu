@@ -220,9 +220,12 @@ cswdg_status read_ctl(cswdg_solver *s, Ctl *h)
     return CSWDG_OK;
 }
 
-cswdg_status write_ctl(cswdg_solver *s, const Ctl *h)
+cswdg_status write_ctl(cswdg_solver *s, const Ctl *hin)
 {
-    CK(cudaMemcpyAsync(s->ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
+    static thread_local Ctl h;
+    h = *hin;
+    h.dtf = (float)h.dt;
+    CK(cudaMemcpyAsync(s->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return CSWDG_OK;
 }

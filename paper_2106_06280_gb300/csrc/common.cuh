@@ -120,7 +120,7 @@ struct Ctl {
     int32_t err;     // sticky error bits
     int32_t nflag;   // flagged-cell count of the last pass
     int32_t active;  // 1: kernels run; 0: step beyond t_end, kernels return
-    int32_t pad;
+    float dtf;       // dt rounded to float (FP32-bulk stage update)
 };
 
 // geometry array indices (REAL, SoA with leading dimension ldc)

@@ -16,8 +16,10 @@ template <int K> struct Ops {
     static constexpr int LH = A4 + ((K == 2) ? 135 : 0); // packed lower Cholesky factor of the beta form
     static constexpr int MI = LH + NM * (NM + 1) / 2;    // [3][2][2] beta_1 gradient maps
     static constexpr int PHI = MI + 12;                  // [NP-1][NM] projection to modes 1..NP-1
-    static constexpr int HB = PHI + (NP - 1) * NM;       // mean side length of the cell
-    static constexpr int SIZE = (HB + 2) & ~1;
+    // linear weights of Step 2 and their use: gamma_{l,3} (3), gamma_{l,5} (4),
+    // 1/gamma_{2,2}, 1/gamma_{3,3}, 1/gamma_{4,5}, gamma_{2,3}, mean side length
+    static constexpr int GAM = PHI + (NP - 1) * NM;
+    static constexpr int SIZE = (GAM + 12 + 1) & ~1;
 };
 
 cudaError_t operator_upload_tables();

@@ -342,7 +342,19 @@ __host__ __device__ int setup_cell(int c, int ld, const double *vtx, const doubl
             }
             op[O::PHI + (i - 1) * NM + j] = 2.0 * s;
         }
-    op[O::HB] = hbar;
+    {
+        // Step 2: gamma_bar_{l,m} = (1/h)^{l-1} normalised over the defined terms
+        const double ih = 1.0 / hbar;
+        const double s2 = 1.0 + ih, s3 = 1.0 + ih + ih * ih, s5 = 1.0 + ih + ih * ih + ih * ih * ih;
+        double *g = op + O::GAM;
+        g[0] = 1.0 / s3; g[1] = ih / s3; g[2] = ih * ih / s3;
+        g[3] = 1.0 / s5; g[4] = ih / s5; g[5] = ih * ih / s5; g[6] = ih * ih * ih / s5;
+        g[7] = s2 / ih;          // 1 / gamma_{2,2}
+        g[8] = s3 / (ih * ih);   // 1 / gamma_{3,3}
+        g[9] = s5 / (ih * ih * ih);  // 1 / gamma_{4,5}
+        g[10] = ih / s3;         // gamma_{2,3}
+        g[11] = hbar;
+    }
     return bad;
 }
 
@@ -401,7 +413,6 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
     int flag = 0;
     if (c < M.nc) {
         const Tab<R, K> &T = ltab<R, K>();
-        const double tl = ctl->t + tfac * ctl->dt;
         R a[NP];
         for (int m = 0; m < NP; ++m) a[m] = u[m * ld + c];
         // cell-mean velocity direction: v = (m_x, m_y) / rho with rho > 0 (Euler),
@@ -452,7 +463,7 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
                     if (code >= 0) {
                         for (int m = 0; m < NP; ++m) uo += w[m] * T.fphi[nf][QF - 1 - g][m];
                     } else {
-                        uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], tl, ui);
+                        uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], ctl->t + tfac * ctl->dt, ui);
                     }
                     J += T.fw[g] * (ui - uo);
                 }
@@ -462,10 +473,19 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
             R nrm2 = R(0);
             for (int m = 0; m < NP; ++m) nrm2 += a[m] * a[m];
             const R kap = M.geo[G_KAPPA * ld + c];
-            // R_j = |num| / (lsum kap sqrt(nrm2)) > C_K, compared in FP64 without division or root
-            // (all factors non-negative; no inflow face or a zero jump never flags)
-            const double den = (double)lsum * (double)kap;
-            flag = (lsum > R(0)) && ((double)num * (double)num > ck * ck * den * den * (double)nrm2);
+            // R_j = |num| / (lsum kap sqrt(nrm2)) > C_K, compared without division or root (all
+            // factors non-negative; no inflow face or a zero jump never flags).  The comparison is
+            // screened in the state precision with a relative margin; close calls are decided in FP64.
+            if (lsum > R(0)) {
+                const R ckr = (R)ck, denr = lsum * kap;
+                const R lhs = num * num, rhs = ckr * ckr * denr * denr * nrm2;
+                if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) {
+                    flag = lhs > rhs;
+                } else {
+                    const double den = (double)lsum * (double)kap;
+                    flag = (double)num * (double)num > ck * ck * den * den * (double)nrm2;
+                }
+            }
         }
         flags[c] = (uint8_t)flag;
     }
@@ -537,18 +557,14 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
             q4[j] = acc;
         }
     }
-    // Step 2: linear weights (1/h)^{l-1}, normalised, and hierarchical polynomials
-    const double ih = 1.0 / (double)op[O::HB];
-    const double s2 = 1.0 + ih, s3 = 1.0 + ih + ih * ih, s5 = 1.0 + ih + ih * ih + ih * ih * ih;
-    const double g22 = ih / s2, g23 = ih / s3, g33 = ih * ih / s3;
-    const double g5[4] = {1.0 / s5, ih / s5, ih * ih / s5, ih * ih * ih / s5};
-    const double g3[3] = {1.0 / s3, g23, g33};
+    // Step 2: hierarchical polynomials with the linear weights precomputed per cell
+    const R *gm = op + O::GAM;
     R p2[NM], p3[NM], p4[NM];
     for (int j = 0; j < NM; ++j) { p2[j] = R(0); p3[j] = R(0); p4[j] = R(0); }
-    for (int j = 0; j < 2; ++j) p2[j] = q2[j] / (R)g22;
-    for (int j = 0; j < 5; ++j) p3[j] = (q3[j] - (R)g23 * p2[j]) / (R)g33;
+    for (int j = 0; j < 2; ++j) p2[j] = q2[j] * gm[7];
+    for (int j = 0; j < 5; ++j) p3[j] = (q3[j] - gm[10] * p2[j]) * gm[8];
     if (K == 2)
-        for (int j = 0; j < 9; ++j) p4[j] = (q4[j] - (R)g5[1] * p2[j] - (R)g5[2] * p3[j]) / (R)g5[3];
+        for (int j = 0; j < 9; ++j) p4[j] = (q4[j] - gm[4] * p2[j] - gm[5] * p3[j]) * gm[9];
     // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2 (sums in FP64)
     double beta[4];
     {
@@ -565,38 +581,46 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
             beta[l + 1] = acc;
         }
     }
-    // beta_1: magnified from the three linear fits through the thirds' centroids (Eqs. sigmaEqn, smoothnessIndicatorT1)
+    // beta_1: magnified from the three linear fits through the thirds' centroids
+    // (Eqs. sigmaEqn, smoothnessIndicatorT1); the sigma-weighted average of the
+    // gradients is formed over a common denominator (one FP64 division)
     {
-        double al[3], bl[3], b1[3];
+        double al[3], bl[3], b1[3], e[3];
         for (int f = 0; f < 3; ++f) {
             const double r1 = (double)t[f][1] - (double)t[f][0], r2 = (double)t[f][2] - (double)t[f][0];
             al[f] = (double)op[O::MI + 4 * f + 0] * r1 + (double)op[O::MI + 4 * f + 1] * r2;
             bl[f] = (double)op[O::MI + 4 * f + 2] * r1 + (double)op[O::MI + 4 * f + 3] * r2;
-            b1[f] = al[f] * al[f] + bl[f] * bl[f];
+            b1[f] = al[f] * al[f] + bl[f] * bl[f];  // beta_{1,l}
+            e[f] = b1[f] + eps;
         }
         const double d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
         const double D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
-        double sg[3], ss = 0.0;
-        for (int f = 0; f < 3; ++f) { sg[f] = (1.0 / 3.0) * (1.0 + D * D / (b1[f] + eps)); ss += sg[f]; }
-        double ab = 0.0, bb = 0.0;
-        for (int f = 0; f < 3; ++f) { ab += sg[f] / ss * al[f]; bb += sg[f] / ss * bl[f]; }
+        const double D2 = D * D;
+        // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
+        const double w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
+        const double inv = 1.0 / (w0 + w1 + w2);
+        const double ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
         beta[0] = ab * ab + bb * bb;
     }
-    // Step 4: tau and nonlinear weights (FP64)
+    // Step 4: tau and nonlinear weights (FP64), normalised over a common denominator
     double om[4];
     if (K == 1) {
         const double e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
         const double tau = (e1 * e1 + e2 * e2) / 4.0;
-        double sw = 0.0;
-        for (int l = 0; l < 3; ++l) { om[l] = g3[l] * (1.0 + tau / (eps + beta[l])); sw += om[l]; }
-        for (int l = 0; l < 3; ++l) om[l] /= sw;
-        om[3] = 0.0;
+        const double a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
+        const double w0 = (double)gm[0] * (a0 + tau) * a1 * a2, w1 = (double)gm[1] * (a1 + tau) * a0 * a2,
+                     w2 = (double)gm[2] * (a2 + tau) * a0 * a1;
+        const double inv = 1.0 / (w0 + w1 + w2);
+        om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = 0.0;
     } else {
         const double e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
         const double tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
-        double sw = 0.0;
-        for (int l = 0; l < 4; ++l) { om[l] = g5[l] * (1.0 + tau / (eps + beta[l])); sw += om[l]; }
-        for (int l = 0; l < 4; ++l) om[l] /= sw;
+        const double a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
+        const double p01 = a[0] * a[1], p23 = a[2] * a[3];
+        const double w[4] = {(double)gm[3] * (a[0] + tau) * a[1] * p23, (double)gm[4] * (a[1] + tau) * a[0] * p23,
+                             (double)gm[5] * (a[2] + tau) * p01 * a[3], (double)gm[6] * (a[3] + tau) * p01 * a[2]};
+        const double inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
+        for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
     }
     // Step 5: combined polynomial (p_1 is the constant cell mean) projected onto modes 1..NP-1
     R cm[NM];

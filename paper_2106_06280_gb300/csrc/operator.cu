@@ -58,8 +58,6 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
     const Tab<R, K> &T = tab<R, K>();
     const int ld = M.ldc;
     const R gam = (R)M.gamma;
-    const double dt = ctl->dt;
-    const double trhs = ctl->t + tfac * dt;
 
     R u[NV][NP], acc[NV][NP];
 #pragma unroll
@@ -120,20 +118,15 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
                 Ui[v] = s;
             }
             if (code >= 0) {
-                // neighbour trace at the same physical point: its local face nf, reversed order;
-                // one branch per face so that the table entries are compile-time constants
-#define CSW_TRACE(NF)                                                                  \
-    _Pragma("unroll") for (int v = 0; v < NV; ++v) {                                  \
-        R s = R(0);                                                                    \
-        _Pragma("unroll") for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[NF][QF - 1 - g][m]; \
-        Uo[v] = s;                                                                     \
-    }
-                if (nf == 0) { CSW_TRACE(0) }
-                else if (nf == 1) { CSW_TRACE(1) }
-                else { CSW_TRACE(2) }
-#undef CSW_TRACE
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R s = R(0);
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[nf][QF - 1 - g][m];
+                    Uo[v] = s;
+                }
             } else {
-                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], trhs, Ui, Uo);
+                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], ctl->t + tfac * ctl->dt, Ui, Uo);
             }
             llf<EQ, R>(Ui, Uo, nx, ny, nl, gam, F);
 #pragma unroll
@@ -145,7 +138,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
         }
     }
 
-    const R cdt = cl * (R)dt;  // one conversion per thread
+    const R cdt = cl * ((sizeof(R) == 4) ? (R)ctl->dtf : (R)ctl->dt);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -220,6 +213,7 @@ __global__ void k_begin_step(Ctl *ctl, int use_cfl)
     if (dt > rem) dt = rem;
     if (!(dt > 0.0)) dt = 0.0;
     ctl->dt = dt;
+    ctl->dtf = (float)dt;
     ctl->active = dt > 0.0;
     ctl->t_next = ctl->t + dt;
     ctl->lam_bits = 0ull;
