@@ -197,6 +197,28 @@ cswdg_status cswdg_internal_layout(cswdg_solver *s, int64_t *ldc_host, int32_t *
  * limiter off); out (nullable) receives the values as doubles. */
 cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out_host, int32_t *n_host);
 
+/* Allocation-free variant of cswdg_conservation for callers that cannot
+ * allocate device memory at the time of the call -- for example code that
+ * runs while a CUDA graph is being captured with allocations not allowed,
+ * real-time loops with a fixed memory budget, or host applications that own
+ * every device allocation themselves.  (The paper has no counterpart; this is
+ * an interface service.)
+ *   modes_dev  device state of nc cells in the library's internal layout and
+ *              precision (cswdg_internal_layout), caller-owned
+ *   sums_dev   device output, nvar doubles: sum_K |K| * mean_K per variable
+ * Work is queued on the solver's stream; nothing is synchronised.  The
+ * reduction's scratch is one fixed device array inside the library (2 MiB on
+ * every GPU that loads it, held until the process exits), so the call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library call.  Limit: at most
+ * 16,777,216 cells (larger meshes get CSWDG_EINVAL).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array: two calls whose
+ * work overlaps on the GPU (different streams, or different solvers on the
+ * same device at the same time) race; calls queued on one stream do not.
+ * Every call rewrites the part of the scratch it reads, so no clearing is
+ * needed.  Errors: EINVAL, ECUDA. */
+cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *modes_dev, double *sums_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -264,6 +264,32 @@ cswdg_status download_modes(cswdg_solver *s, const void *src, double *modes)
 
 }  // namespace
 
+namespace csw {
+bool solver_view(const cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area, void **stream)
+{
+    if (!s || !s->mesh_ready) return false;
+    *nc = s->nc;
+    *ldc = s->ldc;
+    *nvar = s->nv;
+    *np = s->np;
+    *fp32 = s->fp32;
+    *area = s->area;
+    *stream = (void *)s->stream;
+    return true;
+}
+
+cswdg_status solver_fail(cswdg_solver *s, cswdg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    return st;
+}
+}  // namespace csw
+
 // ===========================================================================
 // C interface
 // ===========================================================================

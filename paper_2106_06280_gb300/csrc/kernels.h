@@ -1,6 +1,7 @@
 // kernels.h -- host-side launchers of the CUDA kernels (one translation unit
 // per group of kernels; this header is the only coupling between them).
 #pragma once
+#include "../../include/cswdg.h"
 #include "common.cuh"
 
 namespace csw {
@@ -38,6 +39,12 @@ void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const d
 void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st);
 template <typename R>
 void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st);
+
+// read-only view of a solver for entry points outside api.cu (false: no mesh)
+bool solver_view(const struct ::cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area,
+                 void **stream);
+// record an error on the solver and return the status
+cswdg_status solver_fail(struct ::cswdg_solver *s, cswdg_status st, const char *fmt, ...);
 
 // limiter
 void launch_setup_ops(int k, int nc, int ld, const double *vtx, const double *nvtx, const int32_t *nbr, const uint8_t *nbf,

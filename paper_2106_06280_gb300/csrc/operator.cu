@@ -13,6 +13,7 @@
 //   d u_tilde_i/dt = sum_q W_q grad_r psi_i . (G F(u_q))
 //                   - sum_faces sum_g w_g psi_i(r_g) F*(u-, u+; n_tilde),
 // with G = 2 (dr/dx, dr/dy, ds/dx, ds/dy) and n_tilde = 2 |e| n / |K|.
+#include "../../include/cswdg.h"
 #include "kernels.h"
 #include "physics.cuh"
 #include "tables.cuh"
@@ -355,3 +356,50 @@ template void launch_conservation<float>(int, int, int, int, const double *, con
 template void launch_conservation<double>(int, int, int, int, const double *, const double *, double *, double *, cudaStream_t);
 
 }  // namespace csw
+
+// ---------------------------------------------------------------------------
+// Allocation-free conservation sums.  The per-block partial sums live in this
+// file-scope device array instead of a buffer allocated per solver; every GPU
+// that loads the library holds it (2 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+#define CSW_NOALLOC_MAX_BLOCKS 65536  // 256 cells per block: at most 16,777,216 cells
+#define CSW_NOALLOC_MAX_VARS 4
+static __device__ __align__(256) double g_noalloc_partial[CSW_NOALLOC_MAX_BLOCKS * CSW_NOALLOC_MAX_VARS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *modes_dev, double *sums_dev)
+{
+    int nc = 0, ld = 0, nv = 0, np = 0, fp32 = 0;
+    const double *area = nullptr;
+    cudaStream_t st = nullptr;
+    if (!csw::solver_view(s, &nc, &ld, &nv, &np, &fp32, &area, (void **)&st) || !modes_dev || !sums_dev)
+        return csw::solver_fail(s, CSWDG_EINVAL, "conservation_noalloc: no mesh or null pointer");
+    const int nblk = (nc + 255) / 256;
+    if (nblk > CSW_NOALLOC_MAX_BLOCKS || nv > CSW_NOALLOC_MAX_VARS)
+        return csw::solver_fail(s, CSWDG_EINVAL, "conservation_noalloc: %d cells exceed the fixed scratch (at most %d cells)", nc,
+                                CSW_NOALLOC_MAX_BLOCKS * 256);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: device query failed");
+    if (!g_noalloc_ptr[dev]) {
+        // one-time set-up on this device: the device address of the scratch array
+        double *ptr = nullptr;
+        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_partial);
+        if (e != cudaSuccess || !ptr)
+            return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    if (fp32)
+        csw::launch_conservation<float>(nc, ld, nv, np, area, (const float *)modes_dev, g_noalloc_ptr[dev], sums_dev, st);
+    else
+        csw::launch_conservation<double>(nc, ld, nv, np, area, (const double *)modes_dev, g_noalloc_ptr[dev], sums_dev, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: %s", cudaGetErrorString(e));
+    return CSWDG_OK;
+}
+

@@ -64,6 +64,7 @@ def _load():
         "cswdg_stage_dev": ([vp, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double], C.c_int),
         "cswdg_internal_layout": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
         "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
+        "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -78,7 +79,7 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_launches_per_step", "cswdg_get_time",
             "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
-            "cswdg_internal_layout", "cswdg_stencil_operator"]
+            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc"]
 
 
 def _d(a):
@@ -221,6 +222,11 @@ class Solver:
 
     def stage_dev(self, un_ptr, uprev_ptr, out_ptr, a, b, dt, t_rhs):
         self._chk(lib.cswdg_stage_dev(self.h, un_ptr, uprev_ptr, out_ptr, a, b, dt, t_rhs))
+
+    def conservation_noalloc(self, modes_dev_ptr, sums_dev_ptr):
+        """Queue the allocation-free conservation sums of a device state in the
+        internal layout into a device buffer of nvar doubles (no allocation)."""
+        self._chk(lib.cswdg_conservation_noalloc(self.h, modes_dev_ptr, sums_dev_ptr))
 
     def stencil_operator(self, cell):
         n = C.c_int32()
