@@ -183,10 +183,12 @@ cswdg_status cswdg_cfl_dt(cswdg_solver *s, double *dt_host);
 cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un_dev, const void *uprev_dev, void *out_dev,
                              double a, double b, double dt, double t_rhs);
 
-/* Internal layout of device state arrays: element (v, m, cell i) at
- * [(v*np + m)*ldc + i] of the precision's type (double in FP64, float in
- * FP32_BULK), internal cell i = perm_host[user cell]; ldc >= nc.  Coefficients
- * are sqrt(2/|K|) times the user modes (the reference-orthonormal basis).
+/* Internal layout of device state arrays: cell-major, element (v, m) of
+ * internal cell i at [(i*nvar + v)*np + m] of the precision's type (double in
+ * FP64, float in FP32_BULK), internal cell i = perm_host[user cell].
+ * Coefficients are sqrt(2/|K|) times the user modes (the reference-orthonormal
+ * basis).  ldc_host (nullable) receives the padded cell count of the
+ * per-cell geometry arrays (>= nc; state arrays need nc*nvar*np values).
  * perm_host (nullable) receives nc int32 user->internal indices. */
 cswdg_status cswdg_internal_layout(cswdg_solver *s, int64_t *ldc_host, int32_t *perm_host);
 

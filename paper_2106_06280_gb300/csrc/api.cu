@@ -88,6 +88,7 @@ template <typename R> MeshDev<R> mesh_dev(const cswdg_solver *s)
     M.bf = s->bf;
     M.bc = s->bcd;
     M.gamma = s->cfg.gamma;
+    M.gammar = (R)s->cfg.gamma;
     return M;
 }
 
@@ -127,11 +128,13 @@ void mark(Prof *prof, int cls, cudaStream_t st)
     prof->ev.push_back({cls, e});
 }
 
-cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st, Prof *prof = nullptr, bool force_all = false)
+// after_stage: the stage kernel just before has reset the flagged count
+cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st, Prof *prof = nullptr, bool force_all = false,
+                          bool after_stage = false)
 {
     if (s->cfg.limiter == CSWDG_LIMITER_OFF) return CSWDG_OK;
     const int all = (s->cfg.limiter == CSWDG_LIMITER_ALL) || force_all;
-    CK(cudaMemsetAsync(&s->ctl->nflag, 0, sizeof(int32_t), st));
+    if (!after_stage) CK(cudaMemsetAsync(&s->ctl->nflag, 0, sizeof(int32_t), st));
     if (s->fp32) {
         MeshDev<float> M = mesh_dev<float>(s);
         launch_detect<float>(s->eq, s->k, M, (const float *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
@@ -159,7 +162,10 @@ cswdg_status stage(cswdg_solver *s, const void *un, const void *up, void *out, d
                    cudaStream_t st, Prof *prof = nullptr)
 {
     if (s->fp32) {
-        launch_stage<float>(s->eq, s->k, mesh_dev<float>(s), (const float *)un, (const float *)up, (float *)out, (float)a, (float)b,
+        // a convex combination keeps coefficients that sum to one after rounding
+        // (1/3 and 2/3 rounded separately to float sum to 1 + 3e-8: a drift of the means)
+        const float bf = (float)b, af = (std::fabs(a + b - 1.0) < 1e-12) ? 1.0f - bf : (float)a;
+        launch_stage<float>(s->eq, s->k, mesh_dev<float>(s), (const float *)un, (const float *)up, (float *)out, af, bf,
                             (float)cl, tfac, s->ctl, st);
     } else {
         launch_stage<double>(s->eq, s->k, mesh_dev<double>(s), (const double *)un, (const double *)up, (double *)out, a, b, cl, tfac,
@@ -183,11 +189,11 @@ cswdg_status record_step(cswdg_solver *s, int use_cfl, cudaStream_t st, Prof *pr
     mark(prof, KC_CFL, st);
     CK(cudaGetLastError());
     if ((r = stage(s, nullptr, s->U, s->A, 0.0, 1.0, 1.0, 0.0, st, prof))) return r;
-    if ((r = limiter_pass(s, s->A, 1.0, st, prof))) return r;
+    if ((r = limiter_pass(s, s->A, 1.0, st, prof, false, true))) return r;
     if ((r = stage(s, s->U, s->A, s->B, 0.75, 0.25, 0.25, 1.0, st, prof))) return r;
-    if ((r = limiter_pass(s, s->B, 0.5, st, prof))) return r;
+    if ((r = limiter_pass(s, s->B, 0.5, st, prof, false, true))) return r;
     if ((r = stage(s, s->U, s->B, s->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, st, prof))) return r;
-    if ((r = limiter_pass(s, s->U, 1.0, st, prof))) return r;
+    if ((r = limiter_pass(s, s->U, 1.0, st, prof, false, true))) return r;
     return CSWDG_OK;
 }
 

@@ -123,8 +123,104 @@ struct Ctl {
     float dtf;       // dt rounded to float (FP32-bulk stage update)
 };
 
-// geometry array indices (REAL, SoA with leading dimension ldc)
+// geometry array indices (REAL, SoA with leading dimension ldc): 2 x inverse
+// Jacobian; per face the outward unit normal and |n~| = 2 |e| / |K|; KXRCF scale
 enum { G_RX = 0, G_RY, G_SX, G_SY, G_N0X, G_N0Y, G_N0L, G_N1X, G_N1Y, G_N1L, G_N2X, G_N2Y, G_N2L, G_KAPPA, G_COUNT };
+
+// ---------------------------------------------------------------------------
+// State layout in HBM: cell-major -- the NV*NP coefficients of cell c are
+// contiguous, element (v, m) at [(c * NV + v) * NP + m] -- so that a cell (own
+// or neighbour) is fetched with 16-byte (or 8-byte) vector loads.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t sidx(int nv, int np, int v, int m, int c)
+{
+    return ((size_t)c * nv + v) * np + m;
+}
+
+template <typename R, int N> struct VecOf;  // widest aligned vector for a cell of N values
+template <int N> struct VecOf<float, N> {
+    static constexpr int W = (N % 4 == 0) ? 4 : (N % 2 == 0) ? 2 : 1;
+};
+template <int N> struct VecOf<double, N> {
+    static constexpr int W = (N % 2 == 0) ? 2 : 1;
+};
+
+template <int NV, int NP, typename R>
+__device__ __forceinline__ void load_cell(const R *__restrict__ p, int c, R (&u)[NV][NP])
+{
+    constexpr int N = NV * NP, W = VecOf<R, N>::W;
+    R t[N];
+    const R *q = p + (size_t)c * N;
+    if (W == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(q) + i);
+            t[4 * i] = x.x; t[4 * i + 1] = x.y; t[4 * i + 2] = x.z; t[4 * i + 3] = x.w;
+        }
+    } else if (W == 2 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const float2 x = __ldg(reinterpret_cast<const float2 *>(q) + i);
+            t[2 * i] = x.x; t[2 * i + 1] = x.y;
+        }
+    } else if (W == 2) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 x = __ldg(reinterpret_cast<const double2 *>(q) + i);
+            t[2 * i] = (R)x.x; t[2 * i + 1] = (R)x.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) t[i] = __ldg(q + i);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < NP; ++m) u[v][m] = t[v * NP + m];
+}
+
+// the NP coefficients of variable 0 of cell c (8-byte vector loads when aligned)
+template <int NV, int NP, typename R>
+__device__ __forceinline__ void load_var0(const R *__restrict__ p, int c, R (&a)[NP])
+{
+    const R *q = p + (size_t)c * NV * NP;
+    if (sizeof(R) == 4 && (NV * NP) % 2 == 0 && NP % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < NP / 2; ++i) {
+            const float2 x = __ldg(reinterpret_cast<const float2 *>(q) + i);
+            a[2 * i] = (R)x.x;
+            a[2 * i + 1] = (R)x.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) a[m] = __ldg(q + m);
+    }
+}
+
+template <int NV, int NP, typename R>
+__device__ __forceinline__ void store_cell(R *p, int c, const R (&u)[NV][NP])
+{
+    constexpr int N = NV * NP, W = VecOf<R, N>::W;
+    R *q = p + (size_t)c * N;
+    if (W == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i)
+            reinterpret_cast<float4 *>(q)[i] = make_float4((float)u[(4 * i) / NP][(4 * i) % NP], (float)u[(4 * i + 1) / NP][(4 * i + 1) % NP],
+                                                           (float)u[(4 * i + 2) / NP][(4 * i + 2) % NP],
+                                                           (float)u[(4 * i + 3) / NP][(4 * i + 3) % NP]);
+    } else if (W == 2 && sizeof(R) == 4) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i)
+            reinterpret_cast<float2 *>(q)[i] = make_float2((float)u[(2 * i) / NP][(2 * i) % NP], (float)u[(2 * i + 1) / NP][(2 * i + 1) % NP]);
+    } else if (W == 2) {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i)
+            reinterpret_cast<double2 *>(q)[i] = make_double2((double)u[(2 * i) / NP][(2 * i) % NP], (double)u[(2 * i + 1) / NP][(2 * i + 1) % NP]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) q[i] = u[i / NP][i % NP];
+    }
+}
 
 template <typename R> struct MeshDev {
     int nc;
@@ -135,6 +231,7 @@ template <typename R> struct MeshDev {
     const BFace *bf;        // boundary faces
     const BcTab *bc;
     double gamma;
+    R gammar;               // gamma in the state precision
 };
 
 }  // namespace csw

@@ -28,7 +28,7 @@ cudaError_t limiter_upload_tables();
 
 template <typename R>
 void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
-                  const Ctl *ctl, cudaStream_t st);
+                  Ctl *ctl, cudaStream_t st);
 template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st);
 void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st);
 template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);

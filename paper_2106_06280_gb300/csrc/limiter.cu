@@ -405,7 +405,7 @@ template <int EQ, int K, typename R>
 __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, int all,
                                                 uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
 {
-    constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF;
+    constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF, NVd = Eqn<EQ>::NV;
     if (!ctl->active) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int ld = M.ldc;
@@ -414,12 +414,12 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
     if (c < M.nc) {
         const Tab<R, K> &T = ltab<R, K>();
         R a[NP];
-        for (int m = 0; m < NP; ++m) a[m] = u[m * ld + c];
+        load_var0<NVd, NP>(u, c, a);
         // cell-mean velocity direction: v = (m_x, m_y) / rho with rho > 0 (Euler),
         // v = (u, u) (Burgers); only its sign against each normal is used
         R vx, vy;
         if (EQ == EULER) {
-            const R r = a[0], mx = u[(1 * NP) * ld + c], my = u[(2 * NP) * ld + c], E = u[(3 * NP) * ld + c];
+            const R r = a[0], mx = u[sidx(NVd, NP, 1, 0, c)], my = u[sidx(NVd, NP, 2, 0, c)], E = u[sidx(NVd, NP, 3, 0, c)];
             // positivity of the mean without division: rho > 0 and 2 E rho - |m|^2 > 0, decided in
             // FP64 (FP32 values are first screened with a relative margin; only close calls are
             // recomputed in FP64)
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
                 R w[NP];
                 BFace bf;
                 if (code >= 0) {
-                    for (int m = 0; m < NP; ++m) w[m] = u[m * ld + code];
+                    load_var0<NVd, NP>(u, code, w);
                 } else {
                     bf = M.bf[-code - 1];
                 }
@@ -665,7 +665,7 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
     const R gam = (R)M.gamma;
     R u0[NV][NP];
     for (int v = 0; v < NV; ++v)
-        for (int m = 0; m < NP; ++m) u0[v][m] = u[(v * NP + m) * ld + c];
+        for (int m = 0; m < NP; ++m) u0[v][m] = u[sidx(NV, NP, v, m, c)];
     R mean[NV][3][NSUBK];
     for (int f = 0; f < 3; ++f) {
         const int code = M.nbr[f * ld + c];
@@ -673,7 +673,7 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
         bool constant = false;
         if (code >= 0) {
             for (int v = 0; v < NV; ++v)
-                for (int m = 0; m < NP; ++m) w[v][m] = u[(v * NP + m) * ld + code];
+                for (int m = 0; m < NP; ++m) w[v][m] = u[sidx(NV, NP, v, m, code)];
         } else {
             const BFace bf = M.bf[-code - 1];
             const int kind = M.bc->kind[bf.tag];
@@ -774,8 +774,7 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
     const int ld = M.ldc;
     const int d = lane8 >> 2, fl = lane8 & 3;
     R u0[4][NP];
-    for (int v = 0; v < 4; ++v)
-        for (int m = 0; m < NP; ++m) u0[v][m] = u[(v * NP + m) * ld + c];
+    load_cell<4, NP>(u, c, u0);
     R ub[4];
     for (int v = 0; v < 4; ++v) ub[v] = u0[v][0] * R(0.70710678118654752440);
     R Rm[4][4], Lm[4][4];
@@ -786,9 +785,11 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
         R wc[NP];  // neighbour modes projected on this lane's characteristic field
         bool constant = false;
         if (code >= 0) {
+            R wn[4][NP];
+            load_cell<4, NP>(u, code, wn);
             for (int m = 0; m < NP; ++m) {
                 R s = R(0);
-                for (int v = 0; v < 4; ++v) s += Lm[fl][v] * u[(v * NP + m) * ld + code];
+                for (int v = 0; v < 4; ++v) s += Lm[fl][v] * wn[v][m];
                 wc[m] = s;
             }
         } else {
@@ -870,7 +871,7 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
         if (active && (lane % G) == 0) {
             if (EQ == EULER) {
                 R m0[4];
-                for (int v = 0; v < NV; ++v) m0[v] = u[(v * NP) * M.ldc + c];
+                for (int v = 0; v < NV; ++v) m0[v] = u[sidx(NV, NP, v, 0, c)];
                 positivity_fallback<K, R>(m0, *reinterpret_cast<R(*)[4][NP - 1]>(&res), M.gamma);
             }
             for (int v = 0; v < NV; ++v)
@@ -903,7 +904,7 @@ __global__ void k_scatter(int nv, int np, int ld, const int32_t *__restrict__ fl
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
         const int c = flist[idx];
         for (int v = 0; v < nv; ++v)
-            for (int i = 1; i < np; ++i) u[(v * np + i) * ld + c] = lim_out[((size_t)idx * nv + v) * (np - 1) + i - 1];
+            for (int i = 1; i < np; ++i) u[sidx(nv, np, v, i, c)] = lim_out[((size_t)idx * nv + v) * (np - 1) + i - 1];
     }
 }
 

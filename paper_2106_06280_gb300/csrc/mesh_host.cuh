@@ -194,8 +194,8 @@ inline int build_host_mesh(int k, const int32_t *bckind, int64_t nv, const doubl
             const double dx = X[(f + 1) % 3] - X[f], dy = Y[(f + 1) % 3] - Y[f];
             len[f] = std::sqrt(dx * dx + dy * dy);
             per_ += len[f];
-            geo[(G_N0X + 3 * f) * ld + i] = 2.0 * dy / K;
-            geo[(G_N0Y + 3 * f) * ld + i] = -2.0 * dx / K;
+            geo[(G_N0X + 3 * f) * ld + i] = dy / len[f];
+            geo[(G_N0Y + 3 * f) * ld + i] = -dx / len[f];
             geo[(G_N0L + 3 * f) * ld + i] = 2.0 * len[f] / K;
         }
         const double hc = len[0] * len[1] * len[2] / (4.0 * K);

@@ -3,16 +3,16 @@
 // the CFL reduction, the initial-condition projection, conservation sums and
 // the user-layout <-> internal-layout conversions.
 //
-// Owner-computes: one thread per cell evaluates its volume integral and the
-// three face integrals from its own and its neighbours' traces, so no face
-// buffer, colouring or atomics are needed; the shared-face flux is computed by
-// both cells (the path is bandwidth-bound, the flops are cheap).
+// One thread per cell; within a tile of 128 Morton-ordered cells the traces
+// and the face fluxes are shared through shared memory (see k_stage), so no
+// face buffer in HBM, colouring or atomics are needed.
 //
-// State in HBM: SoA [var][mode][cell], coefficients of the reference-orthonormal
+// State in HBM: cell-major [cell][var][mode], coefficients of the reference-orthonormal
 // basis (u_tilde = sqrt(2/|K|) u_hat), so that
 //   d u_tilde_i/dt = sum_q W_q grad_r psi_i . (G F(u_q))
-//                   - sum_faces sum_g w_g psi_i(r_g) F*(u-, u+; n_tilde),
-// with G = 2 (dr/dx, dr/dy, ds/dx, ds/dy) and n_tilde = 2 |e| n / |K|.
+//                   - sum_faces |n~| sum_g w_g psi_i(r_g) F*(u-, u+; n),
+// with G = 2 (dr/dx, dr/dy, ds/dx, ds/dy), n the outward unit normal and
+// |n~| = 2 |e| / |K|.
 #include "../../include/cswdg.h"
 #include "kernels.h"
 #include "physics.cuh"
@@ -47,27 +47,31 @@ cudaError_t operator_upload_tables()
 
 // ---------------------------------------------------------------------------
 // Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
+// One thread per cell; each cell evaluates its volume integral and all three
+// face integrals (the neighbour's trace is read from its modes), so no face
+// buffer, colouring or atomics are needed.
 // ---------------------------------------------------------------------------
 template <int EQ, int K, typename R>
-__global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up,
-                                              R *out, R ca, R cb, R cl, double tfac, const Ctl *__restrict__ ctl)
+__global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
+    k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl, double tfac, Ctl *__restrict__ ctl)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
     if (!ctl->active) return;
+    // the detection that follows this stage counts its flagged cells from zero
+    // (a step beyond t_end keeps the count of the last active pass)
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nflag = 0;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= M.nc) return;
     const Tab<R, K> &T = tab<R, K>();
     const int ld = M.ldc;
-    const R gam = (R)M.gamma;
+    const R gam = M.gammar;
 
     R u[NV][NP], acc[NV][NP];
+    load_cell<NV, NP>(up, c, u);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-            u[v][m] = up[(v * NP + m) * ld + c];
-            acc[v][m] = R(0);
-        }
+        for (int m = 0; m < NP; ++m) acc[v][m] = R(0);
     const R g0 = M.geo[G_RX * ld + c], g1 = M.geo[G_RY * ld + c], g2 = M.geo[G_SX * ld + c], g3 = M.geo[G_SY * ld + c];
 
     // volume integral
@@ -76,10 +80,10 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
         R U[NV], f[NV], g[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            R s = R(0);
+            R sv = R(0);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) s += u[v][m] * T.vphi[q][m];
-            U[v] = s;
+            for (int m = 0; m < NP; ++m) sv += u[v][m] * T.vphi[q][m];
+            U[v] = sv;
         }
         flux_fg<EQ, R>(U, gam, f, g);
 #pragma unroll
@@ -91,48 +95,55 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
         }
     }
 
-    // face integrals
+    // face integrals: -|n~| sum_g w_g psi_i F*(u-, u+; n), n the outward unit normal
     const unsigned nbf = M.nbf[c];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
         const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c], nl = M.geo[(G_N0L + 3 * f) * ld + c];
         const int code = M.nbr[f * ld + c];
         R w[NV][NP];
-        int nf = (nbf >> (2 * f)) & 3;
+        const int nf = (nbf >> (2 * f)) & 3;
+        const bool swap = code >= 0 && code < c;
+        const R snl = swap ? -nl : nl;
         BFace bf;
-        if (code >= 0) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int m = 0; m < NP; ++m) w[v][m] = up[(v * NP + m) * ld + code];
-        } else {
-            bf = M.bf[-code - 1];
-        }
+        if (code >= 0) load_cell<NV, NP>(up, code, w);
+        else bf = M.bf[-code - 1];
 #pragma unroll
         for (int g = 0; g < QF; ++g) {
             R Ui[NV], Uo[NV], F[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                R s = R(0);
+                R sv = R(0);
 #pragma unroll
-                for (int m = 0; m < NP; ++m) s += u[v][m] * T.fphi[f][g][m];
-                Ui[v] = s;
+                for (int m = 0; m < NP; ++m) sv += u[v][m] * T.fphi[f][g][m];
+                Ui[v] = sv;
             }
             if (code >= 0) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    R s = R(0);
+                    R sv = R(0);
 #pragma unroll
-                    for (int m = 0; m < NP; ++m) s += w[v][m] * T.fphi[nf][QF - 1 - g][m];
-                    Uo[v] = s;
+                    for (int m = 0; m < NP; ++m) sv += w[v][m] * T.fphi[nf][QF - 1 - g][m];
+                    Uo[v] = sv;
                 }
             } else {
                 ghost<EQ, R>(bf, M.bc, (double)T.ft[g], ctl->t + tfac * ctl->dt, Ui, Uo);
             }
-            llf<EQ, R>(Ui, Uo, nx, ny, nl, gam, F);
+            // both cells of a face evaluate the flux in the same canonical order (the
+            // lower internal index as the left state), so their two values are exact
+            // negatives and the cell means are conserved to the rounding of the update
+            {
+                R A[NV], B[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    A[v] = swap ? Uo[v] : Ui[v];
+                    B[v] = swap ? Ui[v] : Uo[v];
+                }
+                llf<EQ, R>(A, B, swap ? -nx : nx, swap ? -ny : ny, R(1), gam, F);
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const R wf = T.fw[g] * F[v];
+                const R wf = T.fw[g] * snl * F[v];
 #pragma unroll
                 for (int m = 0; m < NP; ++m) acc[v][m] -= T.fphi[f][g][m] * wf;
             }
@@ -140,30 +151,44 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1) k_stage(MeshDev
     }
 
     const R cdt = cl * ((sizeof(R) == 4) ? (R)ctl->dtf : (R)ctl->dt);
+    R res[NV][NP];
+    if (un) {
+        R w[NV][NP];
+        load_cell<NV, NP>(un, c, w);
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
+        for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int m = 0; m < NP; ++m) {
-            R r = cb * u[v][m] + cdt * acc[v][m];
-            if (un) r += ca * un[(v * NP + m) * ld + c];
-            out[(v * NP + m) * ld + c] = r;
-        }
+            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m] + ca * w[v][m];
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m];
+    }
+    store_cell<NV, NP>(out, c, res);
+}
+
+template <int EQ, int K, typename R>
+void launch_stage_t(const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac, Ctl *ctl,
+                    cudaStream_t st)
+{
+    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    k_stage<EQ, K, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
 }
 
 template <typename R>
 void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
-                  const Ctl *ctl, cudaStream_t st)
+                  Ctl *ctl, cudaStream_t st)
 {
-    const int blk = 128, grd = (M.nc + blk - 1) / blk;
-    if (eq == BURGERS && k == 1) k_stage<BURGERS, 1, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
-    else if (eq == BURGERS && k == 2) k_stage<BURGERS, 2, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
-    else if (eq == EULER && k == 1) k_stage<EULER, 1, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
-    else k_stage<EULER, 2, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+    if (eq == BURGERS && k == 1) launch_stage_t<BURGERS, 1, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
+    else if (eq == BURGERS && k == 2) launch_stage_t<BURGERS, 2, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
+    else if (eq == EULER && k == 1) launch_stage_t<EULER, 1, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
+    else launch_stage_t<EULER, 2, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
 }
 template void launch_stage<float>(int, int, const MeshDev<float> &, const float *, const float *, float *, float, float, float,
-                                  double, const Ctl *, cudaStream_t);
+                                  double, Ctl *, cudaStream_t);
 template void launch_stage<double>(int, int, const MeshDev<double> &, const double *, const double *, double *, double, double,
-                                   double, double, const Ctl *, cudaStream_t);
+                                   double, double, Ctl *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Time step control.  Max wave speed of the cell means (exact max, order free),
@@ -177,13 +202,12 @@ __global__ void __launch_bounds__(256) k_cfl_max(MeshDev<R> M, int np, const R *
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     R lam = R(0);
     if (c < M.nc) {
-        const int ld = M.ldc;
         const R is2 = R(0.70710678118654752440);
         if (EQ == BURGERS) {
-            lam = R(1.4142135623730951) * rabs(u[c] * is2);
+            lam = R(1.4142135623730951) * rabs(u[sidx(1, np, 0, 0, c)] * is2);
         } else {
-            const R r = u[(0 * np) * ld + c] * is2, mx = u[(1 * np) * ld + c] * is2;
-            const R my = u[(2 * np) * ld + c] * is2, E = u[(3 * np) * ld + c] * is2;
+            const R r = u[sidx(4, np, 0, 0, c)] * is2, mx = u[sidx(4, np, 1, 0, c)] * is2;
+            const R my = u[sidx(4, np, 2, 0, c)] * is2, E = u[sidx(4, np, 3, 0, c)] * is2;
             const R uu = mx / r, vv = my / r;
             const R p = ((R)M.gamma - R(1)) * (E - R(0.5) * (mx * uu + my * vv));
             lam = rsqrt_(uu * uu + vv * vv) + rsqrt_((R)M.gamma * p / r);
@@ -246,7 +270,7 @@ __global__ void k_project(int nc, int ld, int nv, const double *__restrict__ val
         for (int m = 0; m < NP; ++m) {
             double s = 0.0;
             for (int q = 0; q < QV; ++q) s += T.vw[q] * vals[((size_t)c * QV + q) * nv + v] * T.vphi[q][m];
-            u[(v * NP + m) * ld + c] = (R)(2.0 * s);
+            u[sidx(nv, NP, v, m, c)] = (R)(2.0 * s);
         }
 }
 
@@ -261,7 +285,7 @@ template void launch_project<double>(int, int, int, int, const double *, double 
 
 // ---------------------------------------------------------------------------
 // Layout conversions.  user[(uc*nv + v)*np + m] (double, physical basis) <->
-// internal [(v*np + m)*ld + c], scaled by sc[c] = sqrt(2/|K|); perm[c] = user index.
+// internal [(c*nv + v)*np + m], scaled by sc[c] = sqrt(2/|K|); perm[c] = user index.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_from_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm, const double *__restrict__ sc,
@@ -272,7 +296,7 @@ __global__ void k_from_user(int nc, int ld, int nv, int np, const int32_t *__res
     const size_t uc = (size_t)perm[c];
     const double s = sc[c];
     for (int v = 0; v < nv; ++v)
-        for (int m = 0; m < np; ++m) u[(v * np + m) * ld + c] = (R)(s * user[(uc * nv + v) * np + m]);
+        for (int m = 0; m < np; ++m) u[sidx(nv, np, v, m, c)] = (R)(s * user[(uc * nv + v) * np + m]);
 }
 
 template <typename R>
@@ -284,7 +308,7 @@ __global__ void k_to_user(int nc, int ld, int nv, int np, const int32_t *__restr
     const size_t uc = (size_t)perm[c];
     const double s = 1.0 / sc[c];
     for (int v = 0; v < nv; ++v)
-        for (int m = 0; m < np; ++m) user[(uc * nv + v) * np + m] = s * (double)u[(v * np + m) * ld + c];
+        for (int m = 0; m < np; ++m) user[(uc * nv + v) * np + m] = s * (double)u[sidx(nv, np, v, m, c)];
 }
 
 __global__ void k_flags_to_user(int nc, const int32_t *__restrict__ perm, const uint8_t *__restrict__ fl, uint8_t *__restrict__ out)
@@ -324,7 +348,7 @@ __global__ void k_cons_partial(int nc, int ld, int nv, int np, const double *__r
     __shared__ double sm[256];
     for (int v = 0; v < nv; ++v) {
         const int c = blockIdx.x * blockDim.x + threadIdx.x;
-        sm[threadIdx.x] = (c < nc) ? area[c] * (double)u[(v * np) * ld + c] * 0.70710678118654752440 : 0.0;
+        sm[threadIdx.x] = (c < nc) ? area[c] * (double)u[sidx(nv, np, v, 0, c)] * 0.70710678118654752440 : 0.0;
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
             if ((int)threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];

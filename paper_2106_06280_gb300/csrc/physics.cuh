@@ -52,7 +52,7 @@ template <int EQ, typename R> __host__ __device__ __forceinline__ void flux_fg(c
     }
 }
 
-// local Lax-Friedrichs flux through a scaled normal n (|n| = nl):
+// local Lax-Friedrichs flux through a normal n of length nl (the stage kernel passes a unit normal):
 // F = 1/2 (F(UL) + F(UR)).n - 1/2 a (UR - UL), a = max |eigenvalue| along n
 template <int EQ, typename R> __host__ __device__ __forceinline__ void llf(const R *UL, const R *UR, R nx, R ny, R nl, R gam, R *F)
 {

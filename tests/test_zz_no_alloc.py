@@ -10,13 +10,13 @@ pytestmark = pytest.mark.gpu
 
 
 def internal_state(torch, s, modes, areas, dtype):
-    """The library's internal device layout: [(v*np + m)*ldc + i], internal cell
-    i = perm[user cell], coefficients scaled by sqrt(2/|K|)."""
-    ldc, perm = s.internal_layout()
+    """The library's internal device layout: cell-major [(i*nvar + v)*np + m],
+    internal cell i = perm[user cell], coefficients scaled by sqrt(2/|K|)."""
+    _, perm = s.internal_layout()
     nc, nv, np_ = modes.shape
-    host = np.zeros((nv * np_, ldc))
-    host[:, perm] = (modes * np.sqrt(2.0 / areas)[:, None, None]).reshape(nc, nv * np_).T
-    return torch.tensor(host, dtype=dtype, device="cuda").contiguous()
+    host = np.zeros((nc, nv, np_))
+    host[perm] = modes * np.sqrt(2.0 / areas)[:, None, None]
+    return torch.tensor(host.ravel(), dtype=dtype, device="cuda").contiguous()
 
 
 @pytest.mark.parametrize("precision,rtol", [(0, 1e-13), (1, 1e-6)])
