@@ -37,7 +37,18 @@ METRIC = "element-DOF x RK-stage updates/s"
 UNIT = "DOF-stage/s"
 NX, NY, K = 960, 240, 2
 NP, NV = 6, 4
-WORKLOAD = "double Mach reflection, Euler P2, jittered split-square 960x240 (460,800 triangles), KXRCF + CSWENO, SSP-RK3, CFL 0.1"
+WORKLOADS = {
+    "dmr": "double Mach reflection, Euler P2, jittered split-square 960x240 (460,800 triangles), KXRCF + CSWENO, SSP-RK3, CFL 0.1",
+    "ensemble": "256 independent four-quadrant Riemann problems, Euler P2, jittered split-square meshes of 2k-60k triangles "
+                "(4,984,396 triangles in one disconnected mesh), KXRCF + CSWENO, SSP-RK3, CFL 0.1",
+}
+WORKLOAD = WORKLOADS["dmr"]
+
+
+def make_problem(name, seed):
+    if name == "ensemble":
+        return W.riemann_ensemble(256, seed=1000 + 1000 * (seed - 3))
+    return W.double_mach(NX, NY, seed=seed)
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -141,8 +152,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def setup_solver(csw, precision, stream, seed=3):
-    pb = W.double_mach(NX, NY, seed=seed)
+def setup_solver(csw, precision, stream, seed=3, workload="dmr"):
+    pb = make_problem(workload, seed)
     s = csw.Solver(csw.EULER, K, precision, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=stream)
     s.setup(pb)
     s.project_ic(pb.u0, apply_limiter=2)
@@ -162,7 +173,7 @@ def run_ours(args):
     from paper_2106_06280_gb300 import cswdg as csw
 
     stream = torch.cuda.current_stream().cuda_stream
-    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk)
+    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk, workload=args.workload)
     nc = pb.mesh.nc
     t_end = pb.t_end
     s.step(0.0, args.warmup, t_end)
@@ -223,7 +234,7 @@ def run_ours(args):
     fp64 = None
     if args.fp64_steps > 0:
         s.close()
-        pb64, s64 = setup_solver(csw, csw.FP64, stream, seed=3 + rk)
+        pb64, s64 = setup_solver(csw, csw.FP64, stream, seed=3 + rk, workload=args.workload)
         s64.step(0.0, 1, t_end)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -242,10 +253,12 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": nc, "degree": K, "dof_per_cell": NP * NV,
+        "config": {"workload": WORKLOADS[args.workload], "cells": nc, "degree": K, "dof_per_cell": NP * NV,
                    "precision": "FP32 bulk; FP64 smoothness-indicator sums, nonlinear weights, KXRCF test, positivity",
                    "limiter": "KXRCF C_K=1 + CSWENO", "initial_condition": "L2 projection, every cell reconstructed once",
-                   "l2": "inputs larger than L2: per-step working set about 200 MB (three 44 MB state arrays, 24 MB geometry, operator blocks of flagged cells) > 129 MB L2",
+                   "l2": f"inputs larger than L2: per-step working set about {nc * (3 * NP * NV * 4 + 52) / 1e6:.0f} MB "
+                         f"(three {nc * NP * NV * 4 / 1e6:.0f} MB state arrays, {nc * 52 / 1e6:.0f} MB geometry, "
+                         "operator blocks of flagged cells) > 129 MB L2",
                    "replicas": "one independent copy of the workload per GPU" if ws > 1 else None,
                    "flagged_cells_last_pass": nflag},
         "roofline": {"bound": "hbm", "kernel": "k_stage (operator + RK update)", "achieved": achieved, "peak": peak,
@@ -260,18 +273,18 @@ def run_ours(args):
         "fp64": fp64,
     }
     if args.cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample, workload=args.workload)
     s.close()
     return out
 
 
-def cpu_baseline(sample, seed=3):
+def cpu_baseline(sample, seed=3, workload="dmr"):
     """The FP64 oracle as it stands, single thread, on a fixed random sample of
     the cells of the same mesh and initial state: one SSP-RK3 step's work on
     the sample = 3 x (operator on the sample + KXRCF on the sample +
     reconstruction of the flagged sample cells)."""
     import oracle
-    pb = W.double_mach(NX, NY, seed=seed)
+    pb = make_problem(workload, seed)
     o = oracle.Oracle(pb, k=K, limiter=1)
     oa = oracle.Oracle(pb, k=K, limiter=2)
     rng = np.random.default_rng(12345)
@@ -296,7 +309,7 @@ def cpu_baseline(sample, seed=3):
             o.limit_cells(u, flagged)
     dt = time.perf_counter() - t0
     return {"value": sample * NP * NV * 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} random cells of the 460,800-cell mesh at the initial state, one SSP-RK3 step's work "
+            "sample": f"{sample} random cells of the {pb.mesh.nc:,}-cell mesh at the initial state, one SSP-RK3 step's work "
                       f"(3 x operator + KXRCF on the sample, CSWENO on its flagged cells: {nflag // 3} per stage); "
                       f"{dt:.1f} s",
             "seconds": dt}
@@ -312,14 +325,14 @@ def run_reference(args):
     t0 = time.perf_counter()
     cb = None
     for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(args.ref_sample)
+        cb = cpu_baseline(args.ref_sample, workload=args.workload)
         vals.append(cb["value"])
     t1 = time.perf_counter()
     value = float(np.median(vals))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * (t1 - t0) / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "cells": NX * NY * 2, "degree": K},
+            "config": {"workload": WORKLOADS[args.workload], "degree": K},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -330,6 +343,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dmr", choices=sorted(WORKLOADS))
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=3)

@@ -293,3 +293,49 @@ def random_modes(mesh: Mesh, nvar: int, np_: int, seed: int, scale: float = 0.3)
         out[:, :, 0] = base[None, :] * (1.0 + 0.1 * r[:, :, 0])
         out[:, :, 1:] *= 0.2 * np.abs(base)[None, :, None]
     return out * np.sqrt(cell_areas(mesh))[:, None, None]
+
+
+def merge_meshes(meshes, offsets):
+    """Disjoint union of meshes translated by offsets (independent problems
+    advanced as one mesh: no face connects two of them)."""
+    xy, tri, bf = [], [], []
+    nv = 0
+    for m, (ox, oy) in zip(meshes, offsets):
+        xy.append(m.xy + np.array([ox, oy]))
+        tri.append(m.tri + nv)
+        b = m.bface.copy()
+        b[:, :2] += nv
+        bf.append(b)
+        nv += m.nv
+    x0 = min(o[0] for o in offsets)
+    y0 = min(o[1] for o in offsets)
+    return Mesh(xy=np.ascontiguousarray(np.concatenate(xy)), tri=np.ascontiguousarray(np.concatenate(tri).astype(np.int32)),
+                bface=np.ascontiguousarray(np.concatenate(bf).astype(np.int32)), period=None,
+                bounds=(x0, max(o[0] for o in offsets) + 1.0, y0, max(o[1] for o in offsets) + 1.0))
+
+
+def riemann_ensemble(n_meshes: int = 256, total: float = 5.0e6, seed: int = 1000, lo: float = 2.0e3,
+                     hi: float = 6.0e4) -> Problem:
+    """Ensemble of independent four-quadrant Riemann problems (Sec. 4.2
+    Example 7 family) on [0,1]^2, mesh i drawn with seed seed+i: triangle counts
+    log-uniform in [lo, hi], rescaled towards `total` (clamped to [lo, hi]);
+    the meshes are laid out on a 16-wide grid of unit squares 1.5 apart and
+    advanced together as one disconnected mesh with transmissive boundaries."""
+    r = uniform01(seed, np.arange(n_meshes))
+    sizes = np.exp(np.log(lo) + (np.log(hi) - np.log(lo)) * r)
+    sizes = np.clip(sizes * total / sizes.sum(), lo, hi)
+    probs = [riemann_quadrants(max(4, int(round(np.sqrt(sz / 2.0)))), seed + i) for i, sz in enumerate(sizes)]
+    offsets = [(1.5 * (i % 16), 1.5 * (i // 16)) for i in range(n_meshes)]
+    mesh = merge_meshes([p.mesh for p in probs], offsets)
+
+    def u0(x, y):
+        ix = np.clip(np.floor(x / 1.5).astype(int), 0, 15)
+        iy = np.floor(y / 1.5).astype(int)
+        k = iy * 16 + ix
+        out = np.zeros((len(x), 4))
+        for i in np.unique(k):
+            sel = k == i
+            out[sel] = probs[i].u0(x[sel] - offsets[i][0], y[sel] - offsets[i][1])
+        return out
+
+    return Problem("riemann_ensemble", 1, mesh, u0, {2: (TRANSMISSIVE, [])}, 0.25, None)

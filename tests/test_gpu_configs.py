@@ -117,3 +117,24 @@ def test_config3_full_size_sampled_fp64(csw, cuda_stream):
     assert len(flagged) > 10
     lo, st = o.limit_cells(u, flagged, 0.05)
     assert np.abs(ug[flagged] - lo).max() / np.abs(lo).max() < 1e-11
+
+
+def test_config4_small_ensemble_fp64(csw, cuda_stream):
+    """Independent Riemann problems advanced as one disconnected mesh (the
+    ensemble workload's structure, 5 meshes of uneven sizes): 4 steps against
+    the oracle with KXRCF limiting."""
+    pb = W.riemann_ensemble(5, total=3000, seed=2000, lo=200, hi=1200)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    oa = oracle.Oracle(pb, k=2, limiter=2)
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    uo = oa.limit(oa.project(pb.u0), 0.0)[0]
+    s.project_ic(pb.u0, apply_limiter=2)
+    assert np.abs(s.read_modes() - uo).max() / np.abs(uo).max() < 1e-11
+    dt = 0.5 * o.cfl_dt(uo, 0.1)
+    for i in range(4):
+        uo, flo, st = o.step(uo, i * dt, dt)
+    s.step(dt, 4, 1e9)
+    ug = s.read_modes()
+    assert np.array_equal(s.read_flags(), flo) and flo.sum() > 0
+    assert np.abs(ug - uo).max() / np.abs(uo).max() < 1e-11
