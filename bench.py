@@ -254,7 +254,8 @@ def run_ours(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "cells": nc, "degree": K, "dof_per_cell": NP * NV,
-                   "precision": "FP32 bulk; FP64 smoothness-indicator sums, nonlinear weights, KXRCF test, positivity",
+                   "precision": "FP32 state, operator and reconstruction; FP64 for the per-mesh operator blocks and for "
+                                "close calls of the KXRCF and positivity decisions",
                    "limiter": "KXRCF C_K=1 + CSWENO", "initial_condition": "L2 projection, every cell reconstructed once",
                    "l2": f"inputs larger than L2: per-step working set about {nc * (3 * NP * NV * 4 + 52) / 1e6:.0f} MB "
                          f"(three {nc * NP * NV * 4 / 1e6:.0f} MB state arrays, {nc * 52 / 1e6:.0f} MB geometry, "

@@ -123,6 +123,15 @@ struct Ctl {
     float dtf;       // dt rounded to float (FP32-bulk stage update)
 };
 
+// time t + tfac dt of the current stage, for boundary data.  The loads are
+// volatile so that the FP64 arithmetic stays on the (rare) boundary-face path
+// instead of being hoisted into every thread of an FP32 kernel.
+__device__ __forceinline__ double stage_time(const Ctl *ctl, double tfac)
+{
+    const volatile Ctl *v = ctl;
+    return v->t + tfac * v->dt;
+}
+
 // geometry array indices (REAL, SoA with leading dimension ldc): 2 x inverse
 // Jacobian; per face the outward unit normal and |n~| = 2 |e| / |K|; KXRCF scale
 enum { G_RX = 0, G_RY, G_SX, G_SY, G_N0X, G_N0Y, G_N0L, G_N1X, G_N1Y, G_N1L, G_N2X, G_N2Y, G_N2L, G_KAPPA, G_COUNT };

@@ -401,119 +401,114 @@ __device__ __forceinline__ R ghost0(const BFace &bf, const BcTab *bc, double tp,
     return Uin0;  // transmissive, and the wall keeps the density
 }
 
+// KXRCF indicator of cell c (Sec. 2.3): 1 when the jump of the indicator
+// variable over the inflow faces, scaled by h^((k+1)/2) |K|^(1/2) and the L2
+// norm of the cell's polynomial, exceeds C_K.  The modes of the three
+// neighbours are fetched before the inflow test so that all gathers of a
+// thread are in flight together.
 template <int EQ, int K, typename R>
-__global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, int all,
-                                                uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
+__device__ __forceinline__ int detect_cell(const MeshDev<R> &M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, R ck2,
+                                           int all, int c)
 {
     constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF, NVd = Eqn<EQ>::NV;
-    if (!ctl->active) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int ld = M.ldc;
-    const double is2 = 0.70710678118654752440;
+    const Tab<R, K> &T = ltab<R, K>();
+    int code[3];
+    R w[3][NP];
+    R a[NP];
+    load_var0<NVd, NP>(u, c, a);
+    if (!all) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            code[f] = M.nbr[f * ld + c];
+            if (code[f] >= 0) load_var0<NVd, NP>(u, code[f], w[f]);
+        }
+    }
+    // cell-mean velocity direction: v = (m_x, m_y) / rho with rho > 0 (Euler),
+    // v = (u, u) (Burgers); only its sign against each normal is used
+    R vx, vy;
+    if (EQ == EULER) {
+        const R r = a[0], mx = u[sidx(NVd, NP, 1, 0, c)], my = u[sidx(NVd, NP, 2, 0, c)], E = u[sidx(NVd, NP, 3, 0, c)];
+        // positivity of the mean without division: rho > 0 and 2 E rho - |m|^2 > 0, decided in
+        // FP64 (FP32 values are first screened with a relative margin; only close calls are
+        // recomputed in FP64)
+        const R q = R(2) * E * r - (mx * mx + my * my);
+        bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
+        if (!ok && !(q != q)) {
+            const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
+            ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
+        }
+        if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
+        vx = mx;
+        vy = my;
+    } else {
+        vx = vy = a[0];
+        if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+    }
+    if (all) return 1;
+    R num = R(0), lsum = R(0);
+    const unsigned nbfc = M.nbf[c];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c];
+        // inflow test v.n < 0, evaluated without contraction (exact zero for v = (u, u) on n = (a, -a))
+        const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
+        if (!(vn < R(0))) continue;
+        const R nl = M.geo[(G_N0L + 3 * f) * ld + c];
+        const int nf = (nbfc >> (2 * f)) & 3;
+        BFace bf;
+        if (code[f] < 0) bf = M.bf[-code[f] - 1];
+        R J = R(0);
+#pragma unroll
+        for (int g = 0; g < QF; ++g) {
+            R ui = R(0), uo = R(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) ui += a[m] * T.fphi[f][g][m];
+            if (code[f] >= 0) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) uo += w[f][m] * T.fphi[nf][QF - 1 - g][m];
+            } else {
+                uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), ui);
+            }
+            J += T.fw[g] * (ui - uo);
+        }
+        num += nl * J;
+        lsum += nl;
+    }
+    R nrm2 = R(0);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) nrm2 += a[m] * a[m];
+    const R kap = M.geo[G_KAPPA * ld + c];
+    // R_j = |num| / (lsum kap sqrt(nrm2)) > C_K, compared without division or root (all
+    // factors non-negative; no inflow face or a zero jump never flags).  The comparison is
+    // screened in the state precision with a relative margin; close calls are decided in FP64.
     int flag = 0;
-    if (c < M.nc) {
-        const Tab<R, K> &T = ltab<R, K>();
-        R a[NP];
-        load_var0<NVd, NP>(u, c, a);
-        // cell-mean velocity direction: v = (m_x, m_y) / rho with rho > 0 (Euler),
-        // v = (u, u) (Burgers); only its sign against each normal is used
-        R vx, vy;
-        if (EQ == EULER) {
-            const R r = a[0], mx = u[sidx(NVd, NP, 1, 0, c)], my = u[sidx(NVd, NP, 2, 0, c)], E = u[sidx(NVd, NP, 3, 0, c)];
-            // positivity of the mean without division: rho > 0 and 2 E rho - |m|^2 > 0, decided in
-            // FP64 (FP32 values are first screened with a relative margin; only close calls are
-            // recomputed in FP64)
-            const R q = R(2) * E * r - (mx * mx + my * my);
-            bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
-            if (!ok && !(q != q)) {
-                const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
-                ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
-            }
-            if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
-            vx = mx;
-            vy = my;
+    if (lsum > R(0)) {
+        const R denr = lsum * kap;
+        const R lhs = num * num, rhs = ck2 * denr * denr * nrm2;
+        if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) {
+            flag = lhs > rhs;
         } else {
-            vx = vy = a[0];
-            if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+            const double den = (double)lsum * (double)kap;
+            flag = (double)num * (double)num > ck * ck * den * den * (double)nrm2;
         }
-        if (all) {
-            flag = 1;
-        } else {
-            R num = R(0), lsum = R(0);
-            const unsigned nbfc = M.nbf[c];
-            for (int f = 0; f < 3; ++f) {
-                const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c];
-                // inflow test v.n < 0, evaluated without contraction (exact zero for v = (u, u) on n = (a, -a))
-                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
-                if (!(vn < R(0))) continue;
-                const R nl = M.geo[(G_N0L + 3 * f) * ld + c];
-                const int code = M.nbr[f * ld + c];
-                const int nf = (nbfc >> (2 * f)) & 3;
-                R w[NP];
-                BFace bf;
-                if (code >= 0) {
-                    load_var0<NVd, NP>(u, code, w);
-                } else {
-                    bf = M.bf[-code - 1];
-                }
-                R J = R(0);
-                for (int g = 0; g < QF; ++g) {
-                    R ui = R(0), uo = R(0);
-                    for (int m = 0; m < NP; ++m) ui += a[m] * T.fphi[f][g][m];
-                    if (code >= 0) {
-                        for (int m = 0; m < NP; ++m) uo += w[m] * T.fphi[nf][QF - 1 - g][m];
-                    } else {
-                        uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], ctl->t + tfac * ctl->dt, ui);
-                    }
-                    J += T.fw[g] * (ui - uo);
-                }
-                num += nl * J;
-                lsum += nl;
-            }
-            R nrm2 = R(0);
-            for (int m = 0; m < NP; ++m) nrm2 += a[m] * a[m];
-            const R kap = M.geo[G_KAPPA * ld + c];
-            // R_j = |num| / (lsum kap sqrt(nrm2)) > C_K, compared without division or root (all
-            // factors non-negative; no inflow face or a zero jump never flags).  The comparison is
-            // screened in the state precision with a relative margin; close calls are decided in FP64.
-            if (lsum > R(0)) {
-                const R ckr = (R)ck, denr = lsum * kap;
-                const R lhs = num * num, rhs = ckr * ckr * denr * denr * nrm2;
-                if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) {
-                    flag = lhs > rhs;
-                } else {
-                    const double den = (double)lsum * (double)kap;
-                    flag = (double)num * (double)num > ck * ck * den * den * (double)nrm2;
-                }
-            }
-        }
-        flags[c] = (uint8_t)flag;
     }
-    // warp-aggregated compaction
-    const unsigned mask = __ballot_sync(0xffffffffu, flag);
-    if (mask) {
-        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
-    }
+    return flag;
 }
 
-template <typename R>
-void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
-                   int32_t *flist, cudaStream_t st)
+template <int N, typename R>
+__host__ __device__ __forceinline__ R quad_form(const R *__restrict__ L, const R *c)
 {
-    const int blk = 128, grd = (M.nc + blk - 1) / blk;
-    if (eq == BURGERS && k == 1) k_detect<BURGERS, 1, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
-    else if (eq == BURGERS && k == 2) k_detect<BURGERS, 2, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
-    else if (eq == EULER && k == 1) k_detect<EULER, 1, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
-    else k_detect<EULER, 2, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, all, flags, flist);
+    R acc = R(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        R y = R(0);
+#pragma unroll
+        for (int i = j; i < N; ++i) y += L[i * (i + 1) / 2 + j] * c[i];
+        acc += y * y;
+    }
+    return acc;
 }
-template void launch_detect<float>(int, int, const MeshDev<float> &, const float *, Ctl *, double, double, int, uint8_t *, int32_t *,
-                                   cudaStream_t);
-template void launch_detect<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
-                                    int32_t *, cudaStream_t);
 
 // ===========================================================================
 // CSWENO reconstruction of one scalar field (Sec. 3.2 Steps 1-5 / Steps 1-4)
@@ -565,66 +560,104 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
     for (int j = 0; j < 5; ++j) p3[j] = (q3[j] - gm[10] * p2[j]) * gm[8];
     if (K == 2)
         for (int j = 0; j < 9; ++j) p4[j] = (q4[j] - gm[4] * p2[j] - gm[5] * p3[j]) * gm[9];
-    // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2 (sums in FP64)
-    double beta[4];
-    {
-        const R *L = op + O::LH;
-        const int nn[3] = {2, 5, 9};
-        const R *pp[3] = {p2, p3, p4};
-        for (int l = 0; l < Deg<K>::NSLOT - 1; ++l) {
-            double acc = 0.0;
-            for (int j = 0; j < nn[l]; ++j) {
-                R y = R(0);
-                for (int i = j; i < nn[l]; ++i) y += L[i * (i + 1) / 2 + j] * pp[l][i];
-                acc += (double)y * (double)y;
+    // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2 (a sum of squares:
+    // no cancellation, so it is formed in the state precision)
+    R beta[4];
+    beta[1] = quad_form<2>(op + O::LH, p2);
+    beta[2] = quad_form<5>(op + O::LH, p3);
+    if (K == 2) beta[3] = quad_form<9>(op + O::LH, p4);
+    R om[4];
+    if constexpr (sizeof(R) == 8) {
+        // FP64: beta_1 magnified from the three linear fits through the thirds'
+        // centroids (Eqs. sigmaEqn, smoothnessIndicatorT1), the sigma-weighted
+        // average formed over a common denominator (one division)
+        {
+            R al[3], bl[3], b1[3], e[3];
+            for (int f = 0; f < 3; ++f) {
+                const R r1 = t[f][1] - t[f][0], r2 = t[f][2] - t[f][0];
+                al[f] = op[O::MI + 4 * f + 0] * r1 + op[O::MI + 4 * f + 1] * r2;
+                bl[f] = op[O::MI + 4 * f + 2] * r1 + op[O::MI + 4 * f + 3] * r2;
+                b1[f] = al[f] * al[f] + bl[f] * bl[f];  // beta_{1,l}
+                e[f] = b1[f] + R(eps);
             }
-            beta[l + 1] = acc;
+            const R d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
+            const R D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
+            const R D2 = D * D;
+            // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
+            const R w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
+            const R inv = 1.0 / (w0 + w1 + w2);
+            const R ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
+            beta[0] = ab * ab + bb * bb;
         }
-    }
-    // beta_1: magnified from the three linear fits through the thirds' centroids
-    // (Eqs. sigmaEqn, smoothnessIndicatorT1); the sigma-weighted average of the
-    // gradients is formed over a common denominator (one FP64 division)
-    {
-        double al[3], bl[3], b1[3], e[3];
-        for (int f = 0; f < 3; ++f) {
-            const double r1 = (double)t[f][1] - (double)t[f][0], r2 = (double)t[f][2] - (double)t[f][0];
-            al[f] = (double)op[O::MI + 4 * f + 0] * r1 + (double)op[O::MI + 4 * f + 1] * r2;
-            bl[f] = (double)op[O::MI + 4 * f + 2] * r1 + (double)op[O::MI + 4 * f + 3] * r2;
-            b1[f] = al[f] * al[f] + bl[f] * bl[f];  // beta_{1,l}
-            e[f] = b1[f] + eps;
+        // Step 4: tau and nonlinear weights, normalised over a common denominator
+        if (K == 1) {
+            const R e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
+            const R tau = (e1 * e1 + e2 * e2) / 4.0;
+            const R a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
+            const R w0 = gm[0] * (a0 + tau) * a1 * a2, w1 = gm[1] * (a1 + tau) * a0 * a2, w2 = gm[2] * (a2 + tau) * a0 * a1;
+            const R inv = 1.0 / (w0 + w1 + w2);
+            om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = 0.0;
+        } else {
+            const R e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
+            const R tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
+            const R a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
+            const R p01 = a[0] * a[1], p23 = a[2] * a[3];
+            const R w[4] = {gm[3] * (a[0] + tau) * a[1] * p23, gm[4] * (a[1] + tau) * a[0] * p23,
+                            gm[5] * (a[2] + tau) * p01 * a[3], gm[6] * (a[3] + tau) * p01 * a[2]};
+            const R inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
+            for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
         }
-        const double d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
-        const double D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
-        const double D2 = D * D;
-        // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
-        const double w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
-        const double inv = 1.0 / (w0 + w1 + w2);
-        const double ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
-        beta[0] = ab * ab + bb * bb;
-    }
-    // Step 4: tau and nonlinear weights (FP64), normalised over a common denominator
-    double om[4];
-    if (K == 1) {
-        const double e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
-        const double tau = (e1 * e1 + e2 * e2) / 4.0;
-        const double a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
-        const double w0 = (double)gm[0] * (a0 + tau) * a1 * a2, w1 = (double)gm[1] * (a1 + tau) * a0 * a2,
-                     w2 = (double)gm[2] * (a2 + tau) * a0 * a1;
-        const double inv = 1.0 / (w0 + w1 + w2);
-        om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = 0.0;
     } else {
-        const double e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
-        const double tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
-        const double a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
-        const double p01 = a[0] * a[1], p23 = a[2] * a[3];
-        const double w[4] = {(double)gm[3] * (a[0] + tau) * a[1] * p23, (double)gm[4] * (a[1] + tau) * a[0] * p23,
-                             (double)gm[5] * (a[2] + tau) * p01 * a[3], (double)gm[6] * (a[3] + tau) * p01 * a[2]};
-        const double inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
-        for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
+        // FP32: the same weights in quotient form.  Products of three or four
+        // (eps + beta) factors would leave the FP32 range (eps^4 = 1e-40), so each
+        // weight is 1 + X / e_l with X = D^2 or tau; when X >= 1 every weight is
+        // divided by X first (1/X + 1/e_l), which keeps all terms below about 1e10.
+        {
+            R al[3], bl[3], b1[3], ie[3];
+            for (int f = 0; f < 3; ++f) {
+                const R r1 = t[f][1] - t[f][0], r2 = t[f][2] - t[f][0];
+                al[f] = op[O::MI + 4 * f + 0] * r1 + op[O::MI + 4 * f + 1] * r2;
+                bl[f] = op[O::MI + 4 * f + 2] * r1 + op[O::MI + 4 * f + 3] * r2;
+                b1[f] = al[f] * al[f] + bl[f] * bl[f];
+                ie[f] = rrcp(b1[f] + R(eps));
+            }
+            const R d01 = b1[0] - b1[1], d12 = b1[1] - b1[2], d20 = b1[2] - b1[0];
+            const R D = (d01 * d01 + d12 * d12 + d20 * d20) * R(1.0 / 3.0);
+            R s[3];
+            if (D >= R(1)) {
+                const R iD = rrcp(D), iD2 = iD * iD;
+                for (int f = 0; f < 3; ++f) s[f] = iD2 + ie[f];
+            } else {
+                const R D2 = D * D;
+                for (int f = 0; f < 3; ++f) s[f] = R(1) + D2 * ie[f];
+            }
+            const R inv = rrcp(s[0] + s[1] + s[2]);
+            const R ab = (s[0] * al[0] + s[1] * al[1] + s[2] * al[2]) * inv, bb = (s[0] * bl[0] + s[1] * bl[1] + s[2] * bl[2]) * inv;
+            beta[0] = ab * ab + bb * bb;
+        }
+        constexpr int NL = (K == 1) ? 3 : 4;
+        R tau = R(0);
+        for (int l = 0; l < NL - 1; ++l) {
+            const R e = beta[NL - 1] - beta[l];
+            tau += e * e;
+        }
+        tau *= (K == 1) ? R(0.25) : R(1.0 / 16.0);
+        const R *gl = gm + ((K == 1) ? 0 : 3);
+        R w[NL], wsum = R(0);
+        if (tau >= R(1)) {
+            const R it = rrcp(tau);
+            for (int l = 0; l < NL; ++l) w[l] = gl[l] * (it + rrcp(beta[l] + R(eps)));
+        } else {
+            for (int l = 0; l < NL; ++l) w[l] = gl[l] * (R(1) + tau * rrcp(beta[l] + R(eps)));
+        }
+        for (int l = 0; l < NL; ++l) wsum += w[l];
+        const R inv = rrcp(wsum);
+        for (int l = 0; l < NL; ++l) om[l] = w[l] * inv;
+        if (K == 1) om[3] = R(0);
     }
     // Step 5: combined polynomial (p_1 is the constant cell mean) projected onto modes 1..NP-1
     R cm[NM];
-    for (int j = 0; j < NM; ++j) cm[j] = (R)om[1] * p2[j] + (R)om[2] * p3[j] + (R)om[3] * p4[j];
+    for (int j = 0; j < NM; ++j) cm[j] = om[1] * p2[j] + om[2] * p3[j] + om[3] * p4[j];
     for (int i = 0; i < NP - 1; ++i) {
         R acc = R(0);
         for (int j = 0; j < NM; ++j) acc += op[O::PHI + i * NM + j] * cm[j];
@@ -651,6 +684,32 @@ __host__ __device__ __forceinline__ void euler_eig(const R *U, R gam, R nx, R ny
     Lm[1][0] = R(1) - b * q2 * i2c2;              Lm[1][1] = R(2) * b * u * i2c2;     Lm[1][2] = R(2) * b * v * i2c2;     Lm[1][3] = -R(2) * b * i2c2;
     Lm[2][0] = -ut;                               Lm[2][1] = -ny;                     Lm[2][2] = nx;                      Lm[2][3] = R(0);
     Lm[3][0] = (R(0.5) * b * q2 - c * un) * i2c2; Lm[3][1] = -(b * u - c * nx) * i2c2; Lm[3][2] = -(b * v - c * ny) * i2c2; Lm[3][3] = b * i2c2;
+}
+
+// one characteristic field fl of euler_eig: the left eigenvector (row fl of
+// Lm) and the right eigenvector (column fl of Rm), selected without indexing
+// so that the eight-lane limiter keeps them in registers
+template <typename R>
+__host__ __device__ __forceinline__ void euler_eig_field(const R *U, R gam, R nx, R ny, int fl, R (&l)[4], R (&r)[4])
+{
+    const R rho = U[0], u = U[1] / rho, v = U[2] / rho;
+    const R q2 = u * u + v * v;
+    const R p = (gam - R(1)) * (U[3] - R(0.5) * rho * q2);
+    const R c2 = gam * p / rho, c = rsqrt_(c2), H = (U[3] + p) / rho;
+    const R un = u * nx + v * ny, ut = -u * ny + v * nx, b = gam - R(1);
+    const R i2c2 = R(1) / (R(2) * c2);
+    if (fl == 1) {  // entropy
+        r[0] = R(1); r[1] = u; r[2] = v; r[3] = R(0.5) * q2;
+        l[0] = R(1) - b * q2 * i2c2; l[1] = R(2) * b * u * i2c2; l[2] = R(2) * b * v * i2c2; l[3] = -R(2) * b * i2c2;
+    } else if (fl == 2) {  // shear
+        r[0] = R(0); r[1] = -ny; r[2] = nx; r[3] = ut;
+        l[0] = -ut; l[1] = -ny; l[2] = nx; l[3] = R(0);
+    } else {  // acoustic, sg = -1 (fl = 0) or +1 (fl = 3)
+        const R cs = (fl == 0) ? -c : c;
+        r[0] = R(1); r[1] = u + cs * nx; r[2] = v + cs * ny; r[3] = H + cs * un;
+        l[0] = (R(0.5) * b * q2 - cs * un) * i2c2; l[1] = -(b * u - cs * nx) * i2c2; l[2] = -(b * v - cs * ny) * i2c2;
+        l[3] = b * i2c2;
+    }
 }
 
 // reconstructed modes 1..NP-1 of every variable of flagged cell c (Sec. 3.2),
@@ -737,28 +796,36 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
     }
 }
 
-// Euler: a reconstruction with non-positive density or pressure (FP64) at a
-// volume point or a face Gauss point of the cell keeps only the cell mean.
+// Euler: a reconstruction with non-positive density or pressure at a volume
+// point or a face Gauss point of the cell keeps only the cell mean.  The
+// QV + 3 QF points are shared by the eight lanes of the cell (point q on lane
+// q mod 8).  With rho > 0 and gamma > 1, p > 0 is 2 E rho - |m|^2 > 0; that
+// product form is decided in the state precision when it clears a relative
+// margin, and close calls are recomputed in FP64 as (gamma - 1)(E - |m|^2 / 2 rho).
 template <int K, typename R>
-__device__ __forceinline__ void positivity_fallback(const R *mean_modes, R (&res)[4][Deg<K>::NP - 1], double gam)
+__device__ __forceinline__ bool positivity_bad_lane(const R *mean_modes, const R (&res)[4][Deg<K>::NP - 1], int lane8, double gam)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF;
     const Tab<R, K> &T = ltab<R, K>();
     bool bad = false;
-    for (int q = 0; q < QV + 3 * QF && !bad; ++q) {
+    for (int q = lane8; q < QV + 3 * QF; q += 8) {
         const R *phi = (q < QV) ? T.vphi[q] : T.fphi[(q - QV) / QF][(q - QV) % QF];
-        double U[4];
+        R U[4];
         for (int v = 0; v < 4; ++v) {
             R s = mean_modes[v] * phi[0];
             for (int m = 1; m < NP; ++m) s += res[v][m - 1] * phi[m];
-            U[v] = (double)s;
+            U[v] = s;
         }
-        const double p = (gam - 1.0) * (U[3] - 0.5 * (U[1] * U[1] + U[2] * U[2]) / U[0]);
-        if (!(U[0] > 0.0 && p > 0.0)) bad = true;
+        const R two_e_rho = R(2) * U[3] * U[0], m2 = U[1] * U[1] + U[2] * U[2];
+        const R qp = two_e_rho - m2;
+        bool ok = (U[0] > R(0)) && (qp > R(1e-3) * (rabs(two_e_rho) + m2));
+        if (!ok && U[0] > R(0) && !(qp < -R(1e-3) * (rabs(two_e_rho) + m2))) {
+            const double r = (double)U[0], mx = (double)U[1], my = (double)U[2], E = (double)U[3];
+            ok = (gam - 1.0) * (E - 0.5 * (mx * mx + my * my) / r) > 0.0;
+        }
+        bad = bad || !ok;
     }
-    if (bad)
-        for (int v = 0; v < 4; ++v)
-            for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+    return bad;
 }
 
 // Euler: eight lanes per flagged cell, one per (direction d in {x, y},
@@ -777,9 +844,10 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
     load_cell<4, NP>(u, c, u0);
     R ub[4];
     for (int v = 0; v < 4; ++v) ub[v] = u0[v][0] * R(0.70710678118654752440);
-    R Rm[4][4], Lm[4][4];
-    euler_eig<R>(ub, (R)M.gamma, d == 0 ? R(1) : R(0), d == 0 ? R(0) : R(1), Rm, Lm);
+    R Ll[4], Rr[4];
+    euler_eig_field<R>(ub, M.gammar, d == 0 ? R(1) : R(0), d == 0 ? R(0) : R(1), fl, Ll, Rr);
     R tc[3][NSUBK];
+#pragma unroll
     for (int f = 0; f < 3; ++f) {
         const int code = M.nbr[f * ld + c];
         R wc[NP];  // neighbour modes projected on this lane's characteristic field
@@ -789,7 +857,7 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
             load_cell<4, NP>(u, code, wn);
             for (int m = 0; m < NP; ++m) {
                 R s = R(0);
-                for (int v = 0; v < 4; ++v) s += Lm[fl][v] * wn[v][m];
+                for (int v = 0; v < 4; ++v) s += Ll[v] * wn[v][m];
                 wc[m] = s;
             }
         } else {
@@ -799,7 +867,7 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
                 R S[4], dummy[4] = {R(0), R(0), R(0), R(0)};
                 ghost<EULER, R>(bf, M.bc, 0.5, tl, dummy, S);
                 R sc = R(0);
-                for (int v = 0; v < 4; ++v) sc += Lm[fl][v] * S[v];
+                for (int v = 0; v < 4; ++v) sc += Ll[v] * S[v];
                 for (int i = 0; i < NSUBK; ++i) tc[f][i] = sc;
                 constant = true;
             } else {
@@ -811,7 +879,7 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
                         w1 -= R(2) * mn * nx;
                         w2 -= R(2) * mn * ny;
                     }
-                    wc[m] = Lm[fl][0] * u0[0][m] + Lm[fl][1] * w1 + Lm[fl][2] * w2 + Lm[fl][3] * u0[3][m];
+                    wc[m] = Ll[0] * u0[0][m] + Ll[1] * w1 + Ll[2] * w2 + Ll[3] * u0[3][m];
                 }
             }
         }
@@ -823,13 +891,60 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
             }
     }
     R w0 = R(0);
-    for (int v = 0; v < 4; ++v) w0 += Lm[fl][v] * ub[v];
+    for (int v = 0; v < 4; ++v) w0 += Ll[v] * ub[v];
     R md[NP - 1];
     weno_field<K, R>(op, tc, w0, md);
     for (int v = 0; v < 4; ++v)
-        for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0.5) * Rm[v][fl] * md[i];
+        for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0.5) * Rr[v] * md[i];
 }
 
+// KXRCF detection, one thread per cell, and warp-aggregated compaction of the
+// flagged cells into flist (ctl->nflag counts them)
+template <int EQ, int K, typename R>
+__global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, R ck2, int all,
+                                                uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
+{
+    if (!ctl->active) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int flag = 0;
+    if (c < M.nc) {
+        flag = detect_cell<EQ, K, R>(M, u, ctl, tfac, ck, ck2, all, c);
+        flags[c] = (uint8_t)flag;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
+    }
+}
+
+template <typename R>
+void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
+                   int32_t *flist, cudaStream_t st)
+{
+    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    const R ck2 = (R)(ck * ck);  // screening threshold in the state precision
+#define CSW_D(E, KK) k_detect<E, KK, R><<<grd, blk, 0, st>>>(M, u, ctl, tfac, ck, ck2, all, flags, flist)
+    if (eq == BURGERS && k == 1) CSW_D(BURGERS, 1);
+    else if (eq == BURGERS && k == 2) CSW_D(BURGERS, 2);
+    else if (eq == EULER && k == 1) CSW_D(EULER, 1);
+    else CSW_D(EULER, 2);
+#undef CSW_D
+}
+template void launch_detect<float>(int, int, const MeshDev<float> &, const float *, Ctl *, double, double, int, uint8_t *, int32_t *,
+                                   cudaStream_t);
+template void launch_detect<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
+                                    int32_t *, cudaStream_t);
+
+// CSWENO reconstruction of the flagged cells flist[0 .. nflag) into
+// lim_out[idx], from the unlimited state u.  Euler: eight lanes per cell (four
+// cells per warp), contributions summed with shuffles; Burgers: one lane per
+// cell.  The flagged cells are spread over the whole grid (a grid-stride loop
+// over the compacted list), so cells clustered along a shock do not queue up
+// in a few warps.
 template <int EQ, int K, typename R>
 __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
                                                const int32_t *__restrict__ flist, const Ctl *__restrict__ ctl, double tfac,
@@ -839,7 +954,7 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
     constexpr int G = (EQ == EULER) ? 8 : 1;  // lanes per flagged cell
     if (!ctl->active) return;
     const int n = ctl->nflag;
-    const double tl = ctl->t + tfac * ctl->dt;
+    const double tl = stage_time(ctl, tfac);
     const int warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
@@ -848,7 +963,9 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
         const int idx = (base + lane) / G;
         const bool active = idx < n;
         R res[NV][NP - 1];
+#pragma unroll
         for (int v = 0; v < NV; ++v)
+#pragma unroll
             for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
         const int c = active ? flist[idx] : 0;
         if (active) {
@@ -859,7 +976,9 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
                 limit_cell<EQ, K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
         }
         if (EQ == EULER) {
+#pragma unroll
             for (int v = 0; v < NV; ++v)
+#pragma unroll
                 for (int i = 0; i < NP - 1; ++i) {
                     R x = res[v][i];
                     x += __shfl_xor_sync(0xffffffffu, x, 1);
@@ -867,16 +986,22 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
                     x += __shfl_xor_sync(0xffffffffu, x, 4);
                     res[v][i] = x;
                 }
-        }
-        if (active && (lane % G) == 0) {
-            if (EQ == EULER) {
+            bool bad = false;
+            if (active) {
                 R m0[4];
                 for (int v = 0; v < NV; ++v) m0[v] = u[sidx(NV, NP, v, 0, c)];
-                positivity_fallback<K, R>(m0, *reinterpret_cast<R(*)[4][NP - 1]>(&res), M.gamma);
+                bad = positivity_bad_lane<K, R>(m0, *reinterpret_cast<R(*)[4][NP - 1]>(&res), lane & 7, M.gamma);
             }
+            const unsigned grp = (__ballot_sync(0xffffffffu, bad) >> (lane & ~7)) & 0xffu;
+            if (grp)
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+        }
+        if (active && (lane % G) == 0)
             for (int v = 0; v < NV; ++v)
                 for (int i = 0; i < NP - 1; ++i) lim_out[((size_t)idx * NV + v) * (NP - 1) + i] = res[v][i];
-        }
     }
 }
 

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
                     Uo[v] = sv;
                 }
             } else {
-                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], ctl->t + tfac * ctl->dt, Ui, Uo);
+                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), Ui, Uo);
             }
             // both cells of a face evaluate the flux in the same canonical order (the
             // lower internal index as the left state), so their two values are exact

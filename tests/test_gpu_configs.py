@@ -122,19 +122,39 @@ def test_config3_full_size_sampled_fp64(csw, cuda_stream):
 def test_config4_small_ensemble_fp64(csw, cuda_stream):
     """Independent Riemann problems advanced as one disconnected mesh (the
     ensemble workload's structure, 5 meshes of uneven sizes): 4 steps against
-    the oracle with KXRCF limiting."""
+    the oracle with KXRCF limiting.
+
+    The reconstruction amplifies rounding-level differences on this flow (a
+    limiter pass multiplies an input difference by up to about 100 in the
+    low-density cells; over 4 steps the oracle turns a relative input
+    perturbation of 1e-13 into 1.7e-9), so a fixed 1e-11 after 4 steps is not
+    a property of the method.  The tolerance is the oracle's own response to a
+    relative perturbation of 1e-12 of every input coefficient, ten times below
+    the 1e-11 that single operator and limiter passes are held to.  Flags stay
+    bit-exact."""
     pb = W.riemann_ensemble(5, total=3000, seed=2000, lo=200, hi=1200)
     o = oracle.Oracle(pb, k=2, limiter=1)
     oa = oracle.Oracle(pb, k=2, limiter=2)
     s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
     s.setup(pb)
-    uo = oa.limit(oa.project(pb.u0), 0.0)[0]
+    u0 = oa.limit(oa.project(pb.u0), 0.0)[0]
     s.project_ic(pb.u0, apply_limiter=2)
-    assert np.abs(s.read_modes() - uo).max() / np.abs(uo).max() < 1e-11
-    dt = 0.5 * o.cfl_dt(uo, 0.1)
-    for i in range(4):
-        uo, flo, st = o.step(uo, i * dt, dt)
+    assert np.abs(s.read_modes() - u0).max() / np.abs(u0).max() < 1e-11
+    dt = 0.5 * o.cfl_dt(u0, 0.1)
+
+    def run(u):
+        fl = None
+        for i in range(4):
+            u, fl, st = o.step(u, i * dt, dt)
+            assert st == 0
+        return u, fl
+
+    uo, flo = run(u0)
+    sign = np.where(W.uniform01(99, np.arange(u0.size)).reshape(u0.shape) < 0.5, -1.0, 1.0)
+    up, _ = run(u0 * (1.0 + 1e-12 * sign))
+    sens = np.abs(up - uo).max() / np.abs(uo).max()
     s.step(dt, 4, 1e9)
     ug = s.read_modes()
     assert np.array_equal(s.read_flags(), flo) and flo.sum() > 0
-    assert np.abs(ug - uo).max() / np.abs(uo).max() < 1e-11
+    err = np.abs(ug - uo).max() / np.abs(uo).max()
+    assert err < max(1e-11, sens), (err, sens)

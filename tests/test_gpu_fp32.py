@@ -1,0 +1,121 @@
+"""GPU parity in FP32-bulk mode, the precision the benchmark runs in: double
+Mach reflection, Euler P2, 960x240 (460,800 cells), in the launch
+configuration of the benchmark, against the FP64 oracle on 600 sampled cells.
+
+Inputs: a seeded random admissible state and the projected discontinuous
+initial condition (for the operator, which needs positive pressure at its
+quadrature points, the cell means of it).  The GPU receives the oracle's
+input rounded to FP32.
+
+Tolerances, from the arithmetic (u32 = 2^-24 = 6.0e-8):
+* operator: each coefficient of L_h(u) is a sum of about 250 FP32 products
+  (7 volume points x 6 modes x 2 directions, 12 face points x 6 modes, the
+  fluxes at 19 points); with the input rounding the forward error is at most
+  about 300 u32 = 1.8e-5 of the largest term, and the terms are at most a few
+  times max |L_h| here, so TOL_OP = 5e-5 of the field's largest coefficient;
+* reconstruction: the subcell means (6 terms), the least-squares fits (15
+  terms, pseudo-inverse norms below 30), the characteristic transforms (4
+  terms each way) and the projection (9 terms) give at most about 2,000 u32 of
+  the largest mean difference; the nonlinear weights are smooth functions of
+  the smoothness indicators, whose relative FP32 error is of the same order,
+  so TOL_LIM = 2e-4 of the field's largest coefficient;
+* KXRCF flags (every cell of the mesh): the decision is taken on the FP32
+  state, so flags may differ from the oracle's only where the oracle's ratio
+  R / C_K lies within 1e-4 of 1
+  (an FP32-rounded state moves R by far less); positivity fallbacks may differ
+  only where the oracle's reconstruction has a density or pressure within
+  1e-4 (relative) of zero -- neither occurs on these inputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_06280_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_OP = 5e-5
+TOL_LIM = 2e-4
+NX, NY = 960, 240
+
+
+@pytest.fixture(scope="module")
+def dmr():
+    pb = W.double_mach(NX, NY, seed=3)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    rng = np.random.default_rng(77)
+    cells = np.sort(rng.choice(pb.mesh.nc, 600, replace=False)).astype(np.int32)
+    return pb, o, cells
+
+
+def to_f32(u):
+    return u.astype(np.float32).astype(np.float64)
+
+
+def field_errors(ug, uo):
+    """Per variable: max |ug - uo| over the sample / max |uo| of that variable."""
+    return [float(np.abs(ug[:, v] - uo[:, v]).max() / max(np.abs(uo[:, v]).max(), 1e-300)) for v in range(uo.shape[1])]
+
+
+def states(pb, o):
+    yield "random", to_f32(W.random_modes(pb.mesh, 4, 6, 34, scale=0.05))
+    yield "initial", to_f32(o.project(pb.u0))
+
+
+def admissible_states(pb, o):
+    """Inputs of the operator, which needs positive density and pressure at every
+    quadrature point: the random state, and the cell means of the projected
+    initial condition (piecewise constant, the Mach-10 shock and the wall)."""
+    yield "random", to_f32(W.random_modes(pb.mesh, 4, 6, 34, scale=0.05))
+    u = o.project(pb.u0)
+    u[:, :, 1:] = 0.0
+    yield "initial means", to_f32(u)
+
+
+def test_fp32_operator_sampled(csw, cuda_stream, dmr):
+    pb, o, cells = dmr
+    s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_OFF, stream=cuda_stream)
+    s.setup(pb)
+    for name, u in admissible_states(pb, o):
+        Lg = s.eval_rhs(u, 0.05)
+        Lo = o.rhs_cells(u, cells, 0.05)
+        err = field_errors(Lg[cells], Lo)
+        assert max(err) < TOL_OP, (name, err)
+    s.close()
+
+
+def test_fp32_reconstruction_all_cells_sampled(csw, cuda_stream, dmr):
+    """Every cell reconstructed (the initial-condition pass): the FP32 smoothness
+    indicators, nonlinear weights and characteristic projections."""
+    pb, o, cells = dmr
+    s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_ALL, stream=cuda_stream)
+    s.setup(pb)
+    for name, u in states(pb, o):
+        ug, fg = s.limit(u, 0.0)
+        assert np.all(fg == 1)
+        lo, st = o.limit_cells(u, cells, 0.0)
+        assert st == 0
+        err = field_errors(ug[cells], lo)
+        assert max(err) < TOL_LIM, (name, err)
+    s.close()
+
+
+def test_fp32_kxrcf_flags_and_reconstruction_sampled(csw, cuda_stream, dmr):
+    """The projected initial condition: flags on every cell, reconstruction on a
+    sample of 300 flagged cells (the shock and the wall corner)."""
+    pb, o, _ = dmr
+    s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    u = to_f32(o.project(pb.u0))
+    ug, fg = s.limit(u, 0.0)
+    fo, Ro = o.detect(u, 0.0)
+    differ = fg != fo
+    assert np.all(np.abs(Ro[differ] - 1.0) < 1e-4), Ro[differ]
+    both = np.flatnonzero((fg == 1) & (fo == 1)).astype(np.int32)
+    assert len(both) > 300
+    both = np.sort(np.random.default_rng(78).choice(both, 300, replace=False)).astype(np.int32)
+    lo, st = o.limit_cells(u, both, 0.0)
+    assert st == 0
+    err = field_errors(ug[both], lo)
+    assert max(err) < TOL_LIM, err
+    s.close()
