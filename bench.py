@@ -63,12 +63,14 @@ def stage_bytes_per_cell(fp32: bool) -> float:
     """Algorithmic DRAM bytes of the operator + RK stage kernel per cell,
     averaged over the three stages: read u^(i-1) (S), write u^(i) (S), read u^n
     (S, stages 2 and 3), geometry (4 inverse-Jacobian + 9 scaled-normal words),
-    three neighbour indices (12 B) and the packed neighbour faces (1 B).
-    Neighbour traces are reuse of data already counted."""
+    three neighbour indices (12 B), the packed neighbour faces (1 B) and the
+    8 KXRCF precursor words written for the detection.  Neighbour traces are
+    reuse of data already counted."""
     s = 4 if fp32 else 8
     S = NP * NV * s
     geo = 13 * s + 12 + 1
-    return (3 * (2 * S + geo) + 2 * S) / 3.0
+    kx = 8 * s
+    return (3 * (2 * S + geo + kx) + 2 * S) / 3.0
 
 
 def read_peak():
@@ -152,11 +154,19 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def setup_solver(csw, precision, stream, seed=3, workload="dmr"):
+def setup_solver(csw, precision, stream, seed=3, workload="dmr", shape=None):
+    """Mesh, initial condition (projected, every cell reconstructed once) and
+    the stage kernel's launch shape: given, or picked by cswdg_autotune."""
     pb = make_problem(workload, seed)
     s = csw.Solver(csw.EULER, K, precision, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=stream)
     s.setup(pb)
     s.project_ic(pb.u0, apply_limiter=2)
+    if shape:
+        s.set_stage_shape(*shape)
+        s.shape = tuple(shape)
+    else:
+        blk, grid, _ = s.autotune()
+        s.shape = (blk, grid)
     return pb, s
 
 
@@ -173,7 +183,8 @@ def run_ours(args):
     from paper_2106_06280_gb300 import cswdg as csw
 
     stream = torch.cuda.current_stream().cuda_stream
-    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk, workload=args.workload)
+    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk, workload=args.workload, shape=args.stage_shape)
+    shape = s.shape
     nc = pb.mesh.nc
     t_end = pb.t_end
     s.step(0.0, args.warmup, t_end)
@@ -230,22 +241,28 @@ def run_ours(args):
     e2e_value = float(nc) * NP * NV * 3 * e2e_steps * ws / (t1 - t0)
 
     launches = s.launches_per_step(True) * args.steps
-    # FP64 mode on the same workload (secondary)
-    fp64 = None
-    if args.fp64_steps > 0:
-        s.close()
-        pb64, s64 = setup_solver(csw, csw.FP64, stream, seed=3 + rk, workload=args.workload)
-        s64.step(0.0, 1, t_end)
+    s.close()
+
+    def secondary(precision, nsteps, what):
+        """The same workload in another precision mode, device-timed like value."""
+        if nsteps <= 0:
+            return None
+        _, s2 = setup_solver(csw, precision, stream, seed=3 + rk, workload=args.workload, shape=args.stage_shape)
+        s2.step(0.0, args.warmup, t_end)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record()
-        s64.step(0.0, args.fp64_steps, t_end)
+        s2.step(0.0, nsteps, t_end)
         f1.record()
         torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        fp64 = {"value": float(nc) * NP * NV * 3 * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
-                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
-        s64.close()
+        ms2 = f0.elapsed_time(f1)
+        s2.close()
+        return {"value": float(nc) * NP * NV * 3 * nsteps / (ms2 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms2 / nsteps, "steps": nsteps, "precision": what}
+
+    fp32 = secondary(csw.FP32, args.fp32_steps, "FP32 mode: smoothness indicators and nonlinear weights in float as well "
+                                                 "(quotient forms), FP64 only for close calls of the decisions")
+    fp64 = secondary(csw.FP64, args.fp64_steps, "FP64 mode: every step in double")
 
     if rk != 0:
         return None
@@ -254,14 +271,17 @@ def run_ours(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "cells": nc, "degree": K, "dof_per_cell": NP * NV,
-                   "precision": "FP32 state, operator and reconstruction; FP64 for the per-mesh operator blocks and for "
-                                "close calls of the KXRCF and positivity decisions",
+                   "precision": "FP32-bulk mode: FP32 state, operator, RK update and reconstruction polynomials; FP64 "
+                                "smoothness-indicator sums, beta_1, tau and nonlinear weights; KXRCF and positivity "
+                                "decisions screened in FP32, close calls in FP64",
                    "limiter": "KXRCF C_K=1 + CSWENO", "initial_condition": "L2 projection, every cell reconstructed once",
                    "l2": f"inputs larger than L2: per-step working set about {nc * (3 * NP * NV * 4 + 52) / 1e6:.0f} MB "
                          f"(three {nc * NP * NV * 4 / 1e6:.0f} MB state arrays, {nc * 52 / 1e6:.0f} MB geometry, "
                          "operator blocks of flagged cells) > 129 MB L2",
                    "replicas": "one independent copy of the workload per GPU" if ws > 1 else None,
-                   "flagged_cells_last_pass": nflag},
+                   "flagged_cells_last_pass": nflag,
+                   "stage_shape": {"cells_per_block": shape[0], "grid": shape[1] or "one block per tile",
+                                   "chosen_by": "given" if args.stage_shape else "cswdg_autotune"}},
         "roofline": {"bound": "hbm", "kernel": "k_stage (operator + RK update)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_cell_algorithmic": bpc, "stage_ms": stage_ms,
@@ -271,11 +291,11 @@ def run_ours(args):
                 "path": "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)"},
         "gpu_launches": launches,
         "clocks": clk,
+        "fp32_weights": fp32,
         "fp64": fp64,
     }
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample, workload=args.workload)
-    s.close()
     return out
 
 
@@ -348,6 +368,9 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp32-steps", type=int, default=10)
+    ap.add_argument("--stage-shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="cells per block and grid of the stage kernel (e.g. 256,304); default: autotune")
     ap.add_argument("--cpu-sample", type=int, default=200000)
     ap.add_argument("--ref-sample", type=int, default=4000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -44,12 +44,12 @@ typedef enum {
     CSWDG_EMESH = 3,     /* non-conforming mesh, unpaired periodic face, missing tag */
     CSWDG_ENONPHYS = 4,  /* Euler cell mean with rho <= 0 or p <= 0, or a NaN */
     CSWDG_ELSQ = 5,      /* rank-deficient stencil least squares at set-up */
-    CSWDG_ETIMEOUT = 6,  /* reserved: bounded device wait expired */
+    CSWDG_ETIMEOUT = 6,  /* a bounded device wait expired (asynchronous copy into shared memory) */
     CSWDG_ENOMEM = 7     /* device allocation failed */
 } cswdg_status;
 
 enum { CSWDG_BURGERS = 0, CSWDG_EULER = 1 };
-enum { CSWDG_FP64 = 0, CSWDG_FP32_BULK = 1 };
+enum { CSWDG_FP64 = 0, CSWDG_FP32_BULK = 1, CSWDG_FP32 = 2 };
 enum { CSWDG_LIMITER_OFF = 0, CSWDG_LIMITER_KXRCF = 1, CSWDG_LIMITER_ALL = 2 };
 /* Boundary kinds, cswdg_set_boundary. */
 enum {
@@ -65,9 +65,14 @@ typedef struct {
     int32_t equation;  /* CSWDG_BURGERS (Eq. 2dBurgers) or CSWDG_EULER (Eq. 2dEulerEquations) */
     int32_t degree;    /* k in {1, 2}: P^k DG, np = (k+1)(k+2)/2 (Sec. 2) */
     int32_t precision; /* CSWDG_FP64: every step in double.  CSWDG_FP32_BULK: state,
-                          operator and RK update in float with float accumulation;
-                          the troubled-cell test, the smoothness-indicator sums,
-                          the nonlinear weights and the positivity check in double */
+                          operator, RK update and reconstruction polynomials in
+                          float with float accumulation; the smoothness-indicator
+                          sums, beta_1, tau and the nonlinear weights in double; the
+                          troubled-cell and positivity decisions screened in float
+                          and recomputed in double when within a relative 1e-3 of
+                          the threshold.  CSWDG_FP32: as FP32_BULK with the
+                          smoothness indicators and weights in float too (quotient
+                          forms that stay inside the float range) */
     int32_t limiter;   /* CSWDG_LIMITER_*: off, KXRCF-detected cells (Sec. 3.1), every cell */
     double c_k;        /* KXRCF threshold C_K (Sec. 3.1 takes 1) */
     double cfl;        /* time-step factor of the CFL rule used when dt <= 0 */
@@ -138,6 +143,25 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
 cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end,
                                 double *ms_host, int64_t *launches_host);
 
+/* Launch-shape autotuner for the stage kernel (operator + RK update; no
+ * counterpart in the paper).  Times CSWDG_TUNE_CANDIDATES shapes -- cells per
+ * block 64/128/256, one block per tile of cells or a persistent grid of
+ * (SMs x resident blocks) -- on the current state and keeps the fastest for
+ * later steps.  Call after the initial condition is set.  ms_host (nullable,
+ * CSWDG_TUNE_CANDIDATES doubles): mean kernel time of each candidate in the
+ * order 64, 128, 256 (one block per tile), 64 x 8, 128 x 4, 256 x 2,
+ * 128 x 8 blocks per SM; chosen_host (nullable, 2 int32): cells per block and
+ * grid (0 = one block per tile).  The state is not changed.
+ * Errors: EINVAL (no mesh), ECUDA. */
+#define CSWDG_TUNE_CANDIDATES 7
+cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_host);
+
+/* Set the stage kernel's launch shape directly: cells per block (64, 128 or
+ * 256) and the number of blocks (0: one block per tile of cells; > 0: that
+ * many blocks, each looping over tiles).  Results do not depend on the shape.
+ * Errors: EINVAL. */
+cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid);
+
 /* Kernels one cswdg_step step launches (use_cfl: dt <= 0). */
 int32_t cswdg_launches_per_step(const cswdg_solver *s, int32_t use_cfl);
 
@@ -185,7 +209,7 @@ cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un_dev, const void *up
 
 /* Internal layout of device state arrays: cell-major, element (v, m) of
  * internal cell i at [(i*nvar + v)*np + m] of the precision's type (double in
- * FP64, float in FP32_BULK), internal cell i = perm_host[user cell].
+ * FP64, float in FP32_BULK and FP32), internal cell i = perm_host[user cell].
  * Coefficients are sqrt(2/|K|) times the user modes (the reference-orthonormal
  * basis).  ldc_host (nullable) receives the padded cell count of the
  * per-cell geometry arrays (>= nc; state arrays need nc*nvar*np values).

@@ -22,11 +22,13 @@ using namespace csw;
 
 struct cswdg_solver {
     cswdg_config cfg{};
-    int nv = 1, np = 3, k = 1, eq = 0, fp32 = 0;
+    int nv = 1, np = 3, k = 1, eq = 0, fp32 = 0, w32 = 0;
     cudaStream_t stream = nullptr;
     std::string err;
     BcTab bc{};
     bool mesh_ready = false;
+    // the state changed outside a step: ctl->lam_bits does not hold its maximum wave speed
+    bool lam_stale = true;
     int nc = 0, ldc = 0, nbfaces = 0;
     double rmin = 0.0;
     std::vector<int32_t> perm;     // internal -> user
@@ -45,10 +47,13 @@ struct cswdg_solver {
     uint8_t *flags = nullptr, *flags_user = nullptr;
     int32_t *flist = nullptr;
     void *lim_out = nullptr;
+    void *kx = nullptr;  // KXRCF precursors written by the stage kernels of a step
     Ctl *ctl = nullptr;
     double *dev_user = nullptr, *cons_part = nullptr, *cons_out = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int lim_grid = 1;
+    int lim_grid = 1;   // reconstruction kernel: blocks of 128 threads
+    int scat_grid = 1;  // write-back kernel: blocks of 256 threads
+    StageShape shape;   // stage kernel launch shape (cswdg_autotune)
 };
 
 namespace {
@@ -97,10 +102,10 @@ void free_device(cswdg_solver *s)
     for (int i = 0; i < 2; ++i)
         if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
     void *ptrs[] = {s->U, s->A, s->B, s->geo, s->nbr, s->nbf, s->bf, s->bcd, s->dperm, s->sc, s->area, s->ops, s->flags,
-                    s->flags_user, s->flist, s->lim_out, s->ctl, s->dev_user, s->cons_part, s->cons_out};
+                    s->flags_user, s->flist, s->lim_out, s->kx, s->ctl, s->dev_user, s->cons_part, s->cons_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    s->U = s->A = s->B = s->geo = s->ops = s->lim_out = nullptr;
+    s->U = s->A = s->B = s->geo = s->ops = s->lim_out = s->kx = nullptr;
     s->nbr = s->flist = s->dperm = nullptr;
     s->nbf = s->flags = s->flags_user = nullptr;
     s->bf = nullptr;
@@ -137,21 +142,27 @@ cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st
     if (!after_stage) CK(cudaMemsetAsync(&s->ctl->nflag, 0, sizeof(int32_t), st));
     if (s->fp32) {
         MeshDev<float> M = mesh_dev<float>(s);
-        launch_detect<float>(s->eq, s->k, M, (const float *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        if (after_stage)
+            launch_detect_kx<float>(s->eq, s->k, M, (const float *)s->kx, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        else
+            launch_detect<float>(s->eq, s->k, M, (const float *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
         mark(prof, KC_DETECT, st);
         launch_limit<float>(s->eq, s->k, M, (const float *)u, (const float *)s->ops, s->flist, s->ctl, tfac, (float *)s->lim_out,
-                            s->lim_grid, st);
+                            s->lim_grid, s->w32, st);
         mark(prof, KC_LIMIT, st);
-        launch_scatter<float>(s->nv, s->np, s->ldc, s->flist, (const float *)s->lim_out, (float *)u, s->ctl, s->lim_grid, st);
+        launch_scatter<float>(s->nv, s->np, s->ldc, s->flist, (const float *)s->lim_out, (float *)u, s->ctl, s->scat_grid, st);
         mark(prof, KC_SCATTER, st);
     } else {
         MeshDev<double> M = mesh_dev<double>(s);
-        launch_detect<double>(s->eq, s->k, M, (const double *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        if (after_stage)
+            launch_detect_kx<double>(s->eq, s->k, M, (const double *)s->kx, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+        else
+            launch_detect<double>(s->eq, s->k, M, (const double *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
         mark(prof, KC_DETECT, st);
         launch_limit<double>(s->eq, s->k, M, (const double *)u, (const double *)s->ops, s->flist, s->ctl, tfac,
-                             (double *)s->lim_out, s->lim_grid, st);
+                             (double *)s->lim_out, s->lim_grid, 0, st);
         mark(prof, KC_LIMIT, st);
-        launch_scatter<double>(s->nv, s->np, s->ldc, s->flist, (const double *)s->lim_out, (double *)u, s->ctl, s->lim_grid, st);
+        launch_scatter<double>(s->nv, s->np, s->ldc, s->flist, (const double *)s->lim_out, (double *)u, s->ctl, s->scat_grid, st);
         mark(prof, KC_SCATTER, st);
     }
     CK(cudaGetLastError());
@@ -159,17 +170,17 @@ cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st
 }
 
 cswdg_status stage(cswdg_solver *s, const void *un, const void *up, void *out, double a, double b, double cl, double tfac,
-                   cudaStream_t st, Prof *prof = nullptr)
+                   cudaStream_t st, Prof *prof = nullptr, int lam_next = 0, bool write_kx = false)
 {
     if (s->fp32) {
         // a convex combination keeps coefficients that sum to one after rounding
         // (1/3 and 2/3 rounded separately to float sum to 1 + 3e-8: a drift of the means)
         const float bf = (float)b, af = (std::fabs(a + b - 1.0) < 1e-12) ? 1.0f - bf : (float)a;
         launch_stage<float>(s->eq, s->k, mesh_dev<float>(s), (const float *)un, (const float *)up, (float *)out, af, bf,
-                            (float)cl, tfac, s->ctl, st);
+                            (float)cl, tfac, lam_next, write_kx ? (float *)s->kx : nullptr, s->ctl, s->shape, st);
     } else {
         launch_stage<double>(s->eq, s->k, mesh_dev<double>(s), (const double *)un, (const double *)up, (double *)out, a, b, cl, tfac,
-                             s->ctl, st);
+                             lam_next, write_kx ? (double *)s->kx : nullptr, s->ctl, s->shape, st);
     }
     mark(prof, KC_STAGE, st);
     CK(cudaGetLastError());
@@ -178,23 +189,40 @@ cswdg_status stage(cswdg_solver *s, const void *un, const void *up, void *out, d
 
 // One SSP-RK3 step (Table tvd): stage i evaluates L_h at t + (0, dt, dt/2)
 // and the limiter after it sees t + (dt, dt/2, dt).
+// The CFL rule of a step uses the maximum wave speed that the last stage of
+// the previous step folded into ctl->lam_bits (refresh_lam computes it when the
+// state was set from outside).
 cswdg_status record_step(cswdg_solver *s, int use_cfl, cudaStream_t st, Prof *prof = nullptr)
 {
     cswdg_status r;
-    if (use_cfl) {
-        if (s->fp32) launch_cfl<float>(s->eq, mesh_dev<float>(s), s->np, (const float *)s->U, s->ctl, st);
-        else launch_cfl<double>(s->eq, mesh_dev<double>(s), s->np, (const double *)s->U, s->ctl, st);
-    }
     launch_begin_step(s->ctl, use_cfl, st);
     mark(prof, KC_CFL, st);
     CK(cudaGetLastError());
-    if ((r = stage(s, nullptr, s->U, s->A, 0.0, 1.0, 1.0, 0.0, st, prof))) return r;
+    const bool kx = s->cfg.limiter != CSWDG_LIMITER_OFF;
+    if ((r = stage(s, nullptr, s->U, s->A, 0.0, 1.0, 1.0, 0.0, st, prof, 0, kx))) return r;
     if ((r = limiter_pass(s, s->A, 1.0, st, prof, false, true))) return r;
-    if ((r = stage(s, s->U, s->A, s->B, 0.75, 0.25, 0.25, 1.0, st, prof))) return r;
+    if ((r = stage(s, s->U, s->A, s->B, 0.75, 0.25, 0.25, 1.0, st, prof, 0, kx))) return r;
     if ((r = limiter_pass(s, s->B, 0.5, st, prof, false, true))) return r;
-    if ((r = stage(s, s->U, s->B, s->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, st, prof))) return r;
+    if ((r = stage(s, s->U, s->B, s->U, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.5, st, prof, 1, kx))) return r;
     if ((r = limiter_pass(s, s->U, 1.0, st, prof, false, true))) return r;
     return CSWDG_OK;
+}
+
+cswdg_status read_ctl(cswdg_solver *s, Ctl *h);
+cswdg_status write_ctl(cswdg_solver *s, const Ctl *hin);
+
+// maximum wave speed of the current state into ctl->lam_bits (host copy h is
+// updated and written); one launch, counted in *nl
+cswdg_status refresh_lam(cswdg_solver *s, Ctl *h, int64_t *nl)
+{
+    h->lam_bits = 0ull;
+    if (cswdg_status r = write_ctl(s, h)) return r;
+    if (s->fp32) launch_cfl<float>(s->eq, mesh_dev<float>(s), s->np, (const float *)s->U, s->ctl, s->stream);
+    else launch_cfl<double>(s->eq, mesh_dev<double>(s), s->np, (const double *)s->U, s->ctl, s->stream);
+    CK(cudaGetLastError());
+    if (nl) ++*nl;
+    s->lam_stale = false;
+    return read_ctl(s, h);
 }
 
 cswdg_status get_graph(cswdg_solver *s, int use_cfl)
@@ -243,6 +271,12 @@ cswdg_status check_err(cswdg_solver *s, Ctl *h)
         c.err = 0;
         write_ctl(s, &c);
         return fail(s, CSWDG_ENONPHYS, "non-physical cell mean (rho <= 0, p <= 0 or NaN)");
+    }
+    if (h->err & ERR_TIMEOUT) {
+        Ctl c = *h;
+        c.err = 0;
+        write_ctl(s, &c);
+        return fail(s, CSWDG_ETIMEOUT, "bounded device wait expired (operator-block copy)");
     }
     return CSWDG_OK;
 }
@@ -306,7 +340,7 @@ cswdg_status cswdg_create(const cswdg_config *cfg, cswdg_solver **out)
     if (!cfg || !out) return CSWDG_EINVAL;
     *out = nullptr;
     if ((cfg->equation != CSWDG_BURGERS && cfg->equation != CSWDG_EULER) || (cfg->degree != 1 && cfg->degree != 2) ||
-        (cfg->precision != CSWDG_FP64 && cfg->precision != CSWDG_FP32_BULK) || cfg->limiter < 0 || cfg->limiter > 2 ||
+        (cfg->precision != CSWDG_FP64 && cfg->precision != CSWDG_FP32_BULK && cfg->precision != CSWDG_FP32) || cfg->limiter < 0 || cfg->limiter > 2 ||
         !(cfg->gamma > 1.0))
         return CSWDG_EINVAL;
     cswdg_solver *s = new (std::nothrow) cswdg_solver();
@@ -316,7 +350,8 @@ cswdg_status cswdg_create(const cswdg_config *cfg, cswdg_solver **out)
     s->k = cfg->degree;
     s->nv = (s->eq == CSWDG_EULER) ? 4 : 1;
     s->np = (s->k + 1) * (s->k + 2) / 2;
-    s->fp32 = (cfg->precision == CSWDG_FP32_BULK);
+    s->fp32 = (cfg->precision != CSWDG_FP64);
+    s->w32 = (cfg->precision == CSWDG_FP32);
     s->stream = (cudaStream_t)cfg->stream;
     for (int t = 0; t < CSW_MAXTAG; ++t) s->bc.kind[t] = -1;
     if (!tables_ready) {
@@ -401,6 +436,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     A_(dalloc(&s->flags_user, (size_t)ld));
     A_(dalloc(&s->flist, (size_t)ld));
     A_(cudaMalloc(&s->lim_out, (size_t)nc * s->nv * (s->np - 1) * rs));
+    A_(cudaMalloc(&s->kx, (size_t)ld * KX_COUNT * rs));
     A_(dalloc(&s->ctl, 1));
     A_(dalloc(&s->dev_user, std::max((size_t)nc * s->nv * s->np, (size_t)nc * 7 * s->nv)));
     A_(dalloc(&s->cons_part, (size_t)s->nv * ((nc + 255) / 256)));
@@ -422,6 +458,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     CK(cudaMemcpyAsync(s->sc, scv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->area, arv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s->U, 0, nstate * rs, st));
+    s->lam_stale = true;
     CK(cudaMemsetAsync(s->A, 0, nstate * rs, st));
     CK(cudaMemsetAsync(s->B, 0, nstate * rs, st));
     CK(cudaMemsetAsync(s->flags, 0, ld, st));
@@ -444,6 +481,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
             free_device(s);
             return fail(s, CSWDG_ENOMEM, "device allocation (stencil operators): %s", cudaGetErrorString(e));
         }
+        CK(cudaMemsetAsync(dops, 0, (size_t)nc * osz * 8, st));  // padding words included
         CK(cudaMemcpyAsync(dvtx, vtx.data(), vtx.size() * 8, cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(dnvtx, nvtx.data(), nvtx.size() * 8, cudaMemcpyHostToDevice, st));
         // the set-up kernel keeps its QR and Cholesky work arrays on the thread stack
@@ -472,6 +510,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     s->lim_grid = std::max(1, std::min((nc * (s->eq == CSWDG_EULER ? 8 : 1) + 127) / 128, nsm * 16));
+    s->scat_grid = std::max(1, std::min((int)(((long long)nc * s->nv * (s->np - 1) + 255) / 256), nsm * 4));
     s->mesh_ready = true;
     return CSWDG_OK;
 }
@@ -509,6 +548,7 @@ cswdg_status cswdg_project_ic(cswdg_solver *s, const double *values, int32_t app
     CK(cudaMemcpyAsync(s->dev_user, vals.data(), vals.size() * 8, cudaMemcpyHostToDevice, s->stream));
     if (s->fp32) launch_project<float>(s->k, s->nc, s->ldc, s->nv, s->dev_user, (float *)s->U, s->stream);
     else launch_project<double>(s->k, s->nc, s->ldc, s->nv, s->dev_user, (double *)s->U, s->stream);
+    s->lam_stale = true;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     if (apply_limiter && s->cfg.limiter != CSWDG_LIMITER_OFF) {
@@ -539,7 +579,8 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
     h.dt_fixed = dt;
     h.cfl = s->cfg.cfl;
     h.t_end = t_end;
-    h.lam_bits = 0ull;
+    if (use_cfl && s->lam_stale)
+        if (cswdg_status r = refresh_lam(s, &h, nullptr)) return r;
     if (cswdg_status r = write_ctl(s, &h)) return r;
     if (cswdg_status r = get_graph(s, use_cfl)) return r;
     for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(s->graph[use_cfl], s->stream));
@@ -558,10 +599,11 @@ cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, doub
     h.dt_fixed = dt;
     h.cfl = s->cfg.cfl;
     h.t_end = t_end;
-    h.lam_bits = 0ull;
+    int64_t nl = 0;
+    if (use_cfl && s->lam_stale)
+        if (cswdg_status r = refresh_lam(s, &h, &nl)) return r;
     if (cswdg_status r = write_ctl(s, &h)) return r;
     for (int i = 0; i < KC_COUNT; ++i) ms_host[i] = 0.0;
-    int64_t nl = 0;
     for (int64_t it = 0; it < nsteps; ++it) {
         Prof prof;
         mark(&prof, -1, s->stream);
@@ -572,7 +614,7 @@ cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, doub
             cudaEventElapsedTime(&ms, prof.ev[i - 1].second, prof.ev[i].second);
             ms_host[prof.ev[i].first] += ms;
         }
-        nl += (int64_t)prof.ev.size() - 1 + (use_cfl ? 1 : 0);
+        nl += (int64_t)prof.ev.size() - 1;
         for (auto &e : prof.ev) cudaEventDestroy(e.second);
     }
     if (launches_host) *launches_host = nl;
@@ -584,7 +626,8 @@ int32_t cswdg_launches_per_step(const cswdg_solver *s, int32_t use_cfl)
 {
     if (!s) return 0;
     const int lim = (s->cfg.limiter != CSWDG_LIMITER_OFF) ? 3 : 0;
-    return (use_cfl ? 2 : 1) + 3 * (1 + lim);
+    (void)use_cfl;  // the CFL maximum is folded into the last stage
+    return 1 + 3 * (1 + lim);
 }
 
 cswdg_status cswdg_get_time(cswdg_solver *s, double *t)
@@ -615,6 +658,7 @@ cswdg_status cswdg_write_modes(cswdg_solver *s, const double *modes)
 {
     if (!s || !s->mesh_ready || !modes) return fail(s, CSWDG_EINVAL, "write_modes");
     if (cswdg_status r = upload_modes(s, modes, s->U)) return r;
+    s->lam_stale = true;
     CK(cudaStreamSynchronize(s->stream));
     return CSWDG_OK;
 }
@@ -660,6 +704,7 @@ cswdg_status cswdg_eval_rhs(cswdg_solver *s, double t, const double *modes_in, d
     w.active = 1;
     if (cswdg_status r = write_ctl(s, &w)) return r;
     if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    s->lam_stale = true;
     if (cswdg_status r = stage(s, nullptr, s->U, s->A, 0.0, 0.0, 1.0, 0.0, s->stream)) return r;
     if (cswdg_status r = download_modes(s, s->A, rhs)) return r;
     return write_ctl(s, &h);
@@ -677,6 +722,7 @@ cswdg_status cswdg_limit(cswdg_solver *s, double t, const double *modes_in, doub
     w.err = 0;
     if (cswdg_status r = write_ctl(s, &w)) return r;
     if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    s->lam_stale = true;
     if (s->cfg.limiter == CSWDG_LIMITER_OFF) CK(cudaMemsetAsync(s->flags, 0, s->ldc, s->stream));
     if (cswdg_status r = limiter_pass(s, s->U, 0.0, s->stream)) return r;
     if (modes_out)
@@ -752,3 +798,61 @@ cswdg_status cswdg_internal_layout(cswdg_solver *s, int64_t *ldc, int32_t *perm)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Launch-shape autotuner for the stage kernel: times each candidate on the
+// current state (stage into the scratch array B, state untouched) and keeps
+// the fastest.  The step graphs are re-captured with the chosen shape.
+// ---------------------------------------------------------------------------
+cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_host)
+{
+    if (!s || !s->mesh_ready) return fail(s, CSWDG_EINVAL, "autotune: no mesh");
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const StageShape cand[CSWDG_TUNE_CANDIDATES] = {{64, 0},        {128, 0},       {256, 0},      {64, nsm * 8},
+                                                    {128, nsm * 4}, {256, nsm * 2}, {128, nsm * 8}};
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.dt = 0.0;
+    w.active = 1;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int ib = 1;
+    for (int i = 0; i < CSWDG_TUNE_CANDIDATES; ++i) {
+        s->shape = cand[i];
+        for (int it = 0; it < 2; ++it)
+            if (cswdg_status r = stage(s, nullptr, s->U, s->B, 0.0, 1.0, 1.0, 0.0, s->stream)) return r;
+        CK(cudaEventRecord(e0, s->stream));
+        for (int it = 0; it < 5; ++it)
+            if (cswdg_status r = stage(s, nullptr, s->U, s->B, 0.0, 1.0, 1.0, 0.0, s->stream)) return r;
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms_host) ms_host[i] = ms / 5.0;
+        if (ms < best) { best = ms; ib = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->shape = cand[ib];
+    for (int i = 0; i < 2; ++i)
+        if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
+    if (chosen_host) { chosen_host[0] = cand[ib].blk; chosen_host[1] = cand[ib].grid; }
+    return write_ctl(s, &h);
+}
+
+cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid)
+{
+    if (!s || (cells_per_block != 64 && cells_per_block != 128 && cells_per_block != 256) || grid < 0)
+        return fail(s, CSWDG_EINVAL, "set_stage_shape: cells per block 64, 128 or 256; grid >= 0");
+    s->shape.blk = cells_per_block;
+    s->shape.grid = grid;
+    for (int i = 0; i < 2; ++i)
+        if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
+    return CSWDG_OK;
+}

@@ -13,7 +13,7 @@ namespace csw {
 
 enum { BURGERS = 0, EULER = 1 };
 enum { BC_PERIODIC = 0, BC_DIRICHLET = 1, BC_TRANSMISSIVE = 2, BC_WALL = 3, BC_SHOCKLINE = 4 };
-enum { ERR_NONPHYS = 1, ERR_LSQ = 2 };
+enum { ERR_NONPHYS = 1, ERR_LSQ = 2, ERR_TIMEOUT = 4 };
 
 template <int K> struct Deg {
     static constexpr int NP = (K + 1) * (K + 2) / 2;  // modes
@@ -96,6 +96,49 @@ template <typename R, int K> struct Tab {
     R fphi[3][Deg<K>::QF][Deg<K>::NP];// psi_m at the Gauss points of local face f
     R fw[Deg<K>::QF];                 // face weights (sum 1)
     R ft[Deg<K>::QF];                 // Gauss points as edge parameters in [0,1]
+    R fint[3][Deg<K>::NP];            // sum_g fw[g] psi_m(point g of face f): the face mean of psi_m
+};
+
+// Traces seen from the neighbour: psi_m at the Gauss points of local face nf
+// in the reversed order (the adjacent cell's point g is the neighbour's point
+// QF-1-g), in shared memory with rows padded to 16 bytes.  A __constant__
+// table indexed by the per-thread face nf serialises a warp over its distinct
+// faces; a shared-memory row is one or two vector loads.  Every thread of the
+// block calls fill() before the first use (it ends with __syncthreads).
+template <typename R, int K> struct NbrTraceTab {
+    static constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF;
+    static constexpr int W = (sizeof(R) == 4) ? ((NP + 3) & ~3) : ((NP + 1) & ~1);
+    __align__(16) R v[3 * QF * W];
+    __device__ __forceinline__ void fill(const Tab<R, K> &T)
+    {
+        for (int i = threadIdx.x; i < 3 * QF * W; i += blockDim.x) {
+            const int nf = i / (QF * W), g = (i / W) % QF, m = i % W;
+            v[i] = (m < NP) ? T.fphi[nf][QF - 1 - g][m] : R(0);
+        }
+        __syncthreads();
+    }
+    // row of face nf, point g (adjacent cell's order) into registers
+    __device__ __forceinline__ void row(int nf, int g, R (&p)[NP]) const
+    {
+        const R *q = v + (nf * QF + g) * W;
+        if (sizeof(R) == 4) {
+#pragma unroll
+            for (int i = 0; i < W / 4; ++i) {
+                const float4 x = reinterpret_cast<const float4 *>(q)[i];
+                if (4 * i + 0 < NP) p[(4 * i + 0) % NP] = x.x;
+                if (4 * i + 1 < NP) p[(4 * i + 1) % NP] = x.y;
+                if (4 * i + 2 < NP) p[(4 * i + 2) % NP] = x.z;
+                if (4 * i + 3 < NP) p[(4 * i + 3) % NP] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < W / 2; ++i) {
+                const double2 x = reinterpret_cast<const double2 *>(q)[i];
+                if (2 * i + 0 < NP) p[(2 * i + 0) % NP] = (R)x.x;
+                if (2 * i + 1 < NP) p[(2 * i + 1) % NP] = (R)x.y;
+            }
+        }
+    }
 };
 
 // per-boundary-face data (double: used in boundary decisions)
@@ -131,6 +174,12 @@ __device__ __forceinline__ double stage_time(const Ctl *ctl, double tfac)
     const volatile Ctl *v = ctl;
     return v->t + tfac * v->dt;
 }
+
+// KXRCF precursors of a cell, written by the stage kernel for its new state
+// (8 words per cell): the face means of the indicator variable on the three
+// faces, the squared L2 coefficient norm of the indicator variable, and the
+// four (Burgers: one) mean coefficients.
+enum { KX_I0 = 0, KX_I1, KX_I2, KX_NRM2, KX_M0, KX_M1, KX_M2, KX_M3, KX_COUNT };
 
 // geometry array indices (REAL, SoA with leading dimension ldc): 2 x inverse
 // Jacobian; per face the outward unit normal and |n~| = 2 |e| / |K|; KXRCF scale
@@ -228,6 +277,33 @@ __device__ __forceinline__ void store_cell(R *p, int c, const R (&u)[NV][NP])
     } else {
 #pragma unroll
         for (int i = 0; i < N; ++i) q[i] = u[i / NP][i % NP];
+    }
+}
+
+// 8 KXRCF precursor words of cell c (32 or 64 bytes, vector stores / loads)
+template <typename R> __device__ __forceinline__ void store_kx(R *kx, int c, const R (&k8)[KX_COUNT])
+{
+    R *q = kx + (size_t)c * KX_COUNT;
+    if (sizeof(R) == 4) {
+        reinterpret_cast<float4 *>(q)[0] = make_float4((float)k8[0], (float)k8[1], (float)k8[2], (float)k8[3]);
+        reinterpret_cast<float4 *>(q)[1] = make_float4((float)k8[4], (float)k8[5], (float)k8[6], (float)k8[7]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) reinterpret_cast<double2 *>(q)[i] = make_double2((double)k8[2 * i], (double)k8[2 * i + 1]);
+    }
+}
+template <typename R> __device__ __forceinline__ void load_kx(const R *__restrict__ kx, int c, R (&k8)[KX_COUNT])
+{
+    const R *q = kx + (size_t)c * KX_COUNT;
+    if (sizeof(R) == 4) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(q)), b = __ldg(reinterpret_cast<const float4 *>(q) + 1);
+        k8[0] = a.x; k8[1] = a.y; k8[2] = a.z; k8[3] = a.w; k8[4] = b.x; k8[5] = b.y; k8[6] = b.z; k8[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double2 x = __ldg(reinterpret_cast<const double2 *>(q) + i);
+            k8[2 * i] = (R)x.x; k8[2 * i + 1] = (R)x.y;
+        }
     }
 }
 

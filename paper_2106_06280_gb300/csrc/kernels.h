@@ -20,15 +20,21 @@ template <int K> struct Ops {
     // linear weights of Step 2 and their use: gamma_{l,3} (3), gamma_{l,5} (4),
     // 1/gamma_{2,2}, 1/gamma_{3,3}, 1/gamma_{4,5}, gamma_{2,3}, mean side length
     static constexpr int GAM = PHI + (NP - 1) * NM;
-    static constexpr int SIZE = (GAM + 12 + 1) & ~1;
+    // padded to four words: 16-byte rows for the bulk copies into shared memory
+    static constexpr int SIZE = (GAM + 12 + 3) & ~3;
 };
 
 cudaError_t operator_upload_tables();
 cudaError_t limiter_upload_tables();
 
+// launch shape of the stage kernel: cells per block (64, 128, 256) and the
+// number of blocks (0: one block per tile of cells; > 0: a persistent grid)
+struct StageShape {
+    int blk = 128, grid = 0;
+};
 template <typename R>
 void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
-                  Ctl *ctl, cudaStream_t st);
+                  int lam_next, R *kx, Ctl *ctl, StageShape sh, cudaStream_t st);
 template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st);
 void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st);
 template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);
@@ -53,9 +59,14 @@ void launch_ops_to_float(size_t n, const double *src, float *dst, cudaStream_t s
 template <typename R>
 void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
                    int32_t *flist, cudaStream_t st);
+// KXRCF detection from the precursors the stage kernel wrote (kx)
+template <typename R>
+void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *kx, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
+                      int32_t *flist, cudaStream_t st);
+// w32: smoothness indicators and nonlinear weights in float (FP32 mode), else double
 template <typename R>
 void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl,
-                  double tfac, R *lim_out, int grid, cudaStream_t st);
+                  double tfac, R *lim_out, int grid, int w32, cudaStream_t st);
 template <typename R>
 void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st);
 

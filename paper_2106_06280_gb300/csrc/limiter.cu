@@ -408,7 +408,7 @@ __device__ __forceinline__ R ghost0(const BFace &bf, const BcTab *bc, double tp,
 // thread are in flight together.
 template <int EQ, int K, typename R>
 __device__ __forceinline__ int detect_cell(const MeshDev<R> &M, const R *__restrict__ u, Ctl *ctl, double tfac, double ck, R ck2,
-                                           int all, int c)
+                                           int all, int c, const NbrTraceTab<R, K> &ntab)
 {
     constexpr int NP = Deg<K>::NP, QF = Deg<K>::QF, NVd = Eqn<EQ>::NV;
     const int ld = M.ldc;
@@ -465,8 +465,10 @@ __device__ __forceinline__ int detect_cell(const MeshDev<R> &M, const R *__restr
 #pragma unroll
             for (int m = 0; m < NP; ++m) ui += a[m] * T.fphi[f][g][m];
             if (code[f] >= 0) {
+                R ph[NP];
+                ntab.row(nf, g, ph);
 #pragma unroll
-                for (int m = 0; m < NP; ++m) uo += w[f][m] * T.fphi[nf][QF - 1 - g][m];
+                for (int m = 0; m < NP; ++m) uo += w[f][m] * ph[m];
             } else {
                 uo = ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), ui);
             }
@@ -496,16 +498,18 @@ __device__ __forceinline__ int detect_cell(const MeshDev<R> &M, const R *__restr
     return flag;
 }
 
-template <int N, typename R>
-__host__ __device__ __forceinline__ R quad_form(const R *__restrict__ L, const R *c)
+// |L^T c|^2 for the leading N x N block of a packed lower-triangular L; the
+// components in R, the sum of squares accumulated in W
+template <int N, typename R, typename W>
+__host__ __device__ __forceinline__ W quad_form(const R *__restrict__ L, const R *c)
 {
-    R acc = R(0);
+    W acc = W(0);
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         R y = R(0);
 #pragma unroll
         for (int i = j; i < N; ++i) y += L[i * (i + 1) / 2 + j] * c[i];
-        acc += y * y;
+        acc += (W)y * (W)y;
     }
     return acc;
 }
@@ -514,7 +518,9 @@ __host__ __device__ __forceinline__ R quad_form(const R *__restrict__ L, const R
 // CSWENO reconstruction of one scalar field (Sec. 3.2 Steps 1-5 / Steps 1-4)
 // t[f][i]: subcell means of slot f (thirds 0..2, halves 3..6), w0: cell mean.
 // ===========================================================================
-template <int K, typename R>
+// W: precision of the smoothness indicators, tau and the nonlinear weights
+// (double: FP64 and FP32-bulk modes; float: FP32 mode)
+template <int K, typename R, typename W = R>
 __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, const R (&t)[3][Ops<K>::NSUBK], R w0, R (&md)[Deg<K>::NP - 1])
 {
     using O = Ops<K>;
@@ -560,51 +566,52 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
     for (int j = 0; j < 5; ++j) p3[j] = (q3[j] - gm[10] * p2[j]) * gm[8];
     if (K == 2)
         for (int j = 0; j < 9; ++j) p4[j] = (q4[j] - gm[4] * p2[j] - gm[5] * p3[j]) * gm[9];
-    // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2 (a sum of squares:
-    // no cancellation, so it is formed in the state precision)
-    R beta[4];
-    beta[1] = quad_form<2>(op + O::LH, p2);
-    beta[2] = quad_form<5>(op + O::LH, p3);
-    if (K == 2) beta[3] = quad_form<9>(op + O::LH, p4);
-    R om[4];
-    if constexpr (sizeof(R) == 8) {
+    // Step 3: smoothness indicators beta_l = |L^T c(p_l)|^2, summed in W
+    W beta[4];
+    beta[1] = quad_form<2, R, W>(op + O::LH, p2);
+    beta[2] = quad_form<5, R, W>(op + O::LH, p3);
+    if (K == 2) beta[3] = quad_form<9, R, W>(op + O::LH, p4);
+    W om[4];
+    if constexpr (sizeof(W) == 8) {
         // FP64: beta_1 magnified from the three linear fits through the thirds'
         // centroids (Eqs. sigmaEqn, smoothnessIndicatorT1), the sigma-weighted
         // average formed over a common denominator (one division)
         {
-            R al[3], bl[3], b1[3], e[3];
+            // the gradients of p_{1,l} are stencil polynomials like p_l (state
+            // precision); beta_{1,l} and everything after it in W
+            W al[3], bl[3], b1[3], e[3];
             for (int f = 0; f < 3; ++f) {
                 const R r1 = t[f][1] - t[f][0], r2 = t[f][2] - t[f][0];
-                al[f] = op[O::MI + 4 * f + 0] * r1 + op[O::MI + 4 * f + 1] * r2;
-                bl[f] = op[O::MI + 4 * f + 2] * r1 + op[O::MI + 4 * f + 3] * r2;
+                al[f] = (W)(op[O::MI + 4 * f + 0] * r1 + op[O::MI + 4 * f + 1] * r2);
+                bl[f] = (W)(op[O::MI + 4 * f + 2] * r1 + op[O::MI + 4 * f + 3] * r2);
                 b1[f] = al[f] * al[f] + bl[f] * bl[f];  // beta_{1,l}
-                e[f] = b1[f] + R(eps);
+                e[f] = b1[f] + W(eps);
             }
-            const R d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
-            const R D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
-            const R D2 = D * D;
+            const W d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
+            const W D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
+            const W D2 = D * D;
             // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
-            const R w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
-            const R inv = 1.0 / (w0 + w1 + w2);
-            const R ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
+            const W w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
+            const W inv = 1.0 / (w0 + w1 + w2);
+            const W ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
             beta[0] = ab * ab + bb * bb;
         }
         // Step 4: tau and nonlinear weights, normalised over a common denominator
         if (K == 1) {
-            const R e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
-            const R tau = (e1 * e1 + e2 * e2) / 4.0;
-            const R a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
-            const R w0 = gm[0] * (a0 + tau) * a1 * a2, w1 = gm[1] * (a1 + tau) * a0 * a2, w2 = gm[2] * (a2 + tau) * a0 * a1;
-            const R inv = 1.0 / (w0 + w1 + w2);
-            om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = 0.0;
+            const W e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
+            const W tau = (e1 * e1 + e2 * e2) / 4.0;
+            const W a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
+            const W w0 = (W)gm[0] * (a0 + tau) * a1 * a2, w1 = (W)gm[1] * (a1 + tau) * a0 * a2, w2 = (W)gm[2] * (a2 + tau) * a0 * a1;
+            const W inv = 1.0 / (w0 + w1 + w2);
+            om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = W(0);
         } else {
-            const R e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
-            const R tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
-            const R a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
-            const R p01 = a[0] * a[1], p23 = a[2] * a[3];
-            const R w[4] = {gm[3] * (a[0] + tau) * a[1] * p23, gm[4] * (a[1] + tau) * a[0] * p23,
-                            gm[5] * (a[2] + tau) * p01 * a[3], gm[6] * (a[3] + tau) * p01 * a[2]};
-            const R inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
+            const W e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
+            const W tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
+            const W a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
+            const W p01 = a[0] * a[1], p23 = a[2] * a[3];
+            const W w[4] = {(W)gm[3] * (a[0] + tau) * a[1] * p23, (W)gm[4] * (a[1] + tau) * a[0] * p23,
+                            (W)gm[5] * (a[2] + tau) * p01 * a[3], (W)gm[6] * (a[3] + tau) * p01 * a[2]};
+            const W inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
             for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
         }
     } else {
@@ -657,7 +664,7 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
     }
     // Step 5: combined polynomial (p_1 is the constant cell mean) projected onto modes 1..NP-1
     R cm[NM];
-    for (int j = 0; j < NM; ++j) cm[j] = om[1] * p2[j] + om[2] * p3[j] + om[3] * p4[j];
+    for (int j = 0; j < NM; ++j) cm[j] = (R)om[1] * p2[j] + (R)om[2] * p3[j] + (R)om[3] * p4[j];
     for (int i = 0; i < NP - 1; ++i) {
         R acc = R(0);
         for (int j = 0; j < NM; ++j) acc += op[O::PHI + i * NM + j] * cm[j];
@@ -714,7 +721,7 @@ __host__ __device__ __forceinline__ void euler_eig_field(const R *U, R gam, R nx
 
 // reconstructed modes 1..NP-1 of every variable of flagged cell c (Sec. 3.2),
 // from the unlimited state u, at limiter time tl
-template <int EQ, int K, typename R>
+template <int EQ, int K, typename R, typename W = R>
 __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R *u, const R *op, int c, double tl,
                                                     R (&res)[Eqn<EQ>::NV][Deg<K>::NP - 1])
 {
@@ -769,7 +776,7 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
     for (int v = 0; v < NV; ++v) ub[v] = u0[v][0] * R(0.70710678118654752440);
     if (EQ == BURGERS) {
         R md[NP - 1];
-        weno_field<K, R>(op, mean[0], ub[0], md);
+        weno_field<K, R, W>(op, mean[0], ub[0], md);
         for (int i = 0; i < NP - 1; ++i) res[0][i] = md[i];
     } else {
         for (int v = 0; v < NV; ++v)
@@ -788,7 +795,7 @@ __host__ __device__ __forceinline__ void limit_cell(const MeshDev<R> &M, const R
                 R w0 = R(0);
                 for (int v = 0; v < 4; ++v) w0 += Lm[fl][v] * ub[v];
                 R md[NP - 1];
-                weno_field<K, R>(op, tc, w0, md);
+                weno_field<K, R, W>(op, tc, w0, md);
                 for (int v = 0; v < 4; ++v)
                     for (int i = 0; i < NP - 1; ++i) res[v][i] += R(0.5) * Rm[v][fl] * md[i];
             }
@@ -832,7 +839,7 @@ __device__ __forceinline__ bool positivity_bad_lane(const R *mean_modes, const R
 // characteristic field); each lane transforms the neighbours' modes into its
 // field, forms the subcell means, reconstructs (weno_field) and maps back by
 // the right eigenvectors; the eight contributions are summed with shuffles.
-template <int K, typename R>
+template <int K, typename R, typename W = R>
 __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const R *__restrict__ u, const R *__restrict__ op, int c,
                                                       double tl, int lane8, R (&res)[4][Deg<K>::NP - 1])
 {
@@ -893,7 +900,7 @@ __device__ __forceinline__ void limit_cell_euler_lane(const MeshDev<R> &M, const
     R w0 = R(0);
     for (int v = 0; v < 4; ++v) w0 += Ll[v] * ub[v];
     R md[NP - 1];
-    weno_field<K, R>(op, tc, w0, md);
+    weno_field<K, R, W>(op, tc, w0, md);
     for (int v = 0; v < 4; ++v)
         for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0.5) * Rr[v] * md[i];
 }
@@ -905,10 +912,12 @@ __global__ void __launch_bounds__(128) k_detect(MeshDev<R> M, const R *__restric
                                                 uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
 {
     if (!ctl->active) return;
+    __shared__ NbrTraceTab<R, K> ntab;
+    ntab.fill(ltab<R, K>());
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     int flag = 0;
     if (c < M.nc) {
-        flag = detect_cell<EQ, K, R>(M, u, ctl, tfac, ck, ck2, all, c);
+        flag = detect_cell<EQ, K, R>(M, u, ctl, tfac, ck, ck2, all, c, ntab);
         flags[c] = (uint8_t)flag;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, flag);
@@ -939,13 +948,185 @@ template void launch_detect<float>(int, int, const MeshDev<float> &, const float
 template void launch_detect<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
                                     int32_t *, cudaStream_t);
 
+// KXRCF detection inside a time step, from the precursors the stage kernel
+// wrote for its output (kx: face means, coefficient norm and means of each
+// cell).  The Gauss-rule jump integral over face f, divided by the face
+// length, is the cell's face mean minus the neighbour's face mean on the same
+// face (a face mean does not depend on the orientation of the points); on boundary
+// faces the ghost is integrated at the Gauss points as in detect_cell.  The
+// decision is the same product form, screened in the state precision, with
+// FP64 close calls.
+template <int EQ, int K, typename R>
+__global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__restrict__ kx, Ctl *ctl, double tfac, double ck, R ck2,
+                                                   int all, uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
+{
+    constexpr int QF = Deg<K>::QF;
+    if (!ctl->active) return;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int flag = 0;
+    if (c < M.nc) {
+        const int ld = M.ldc;
+        // every load of the thread is issued before the first use: the neighbour
+        // ids and their face means (one dependent level), the own precursors and
+        // the geometry
+        int code[3];
+        R Io[3], gn[3][3], kap = R(0);
+        if (!all) {
+            const unsigned nbfc = M.nbf[c];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) code[f] = M.nbr[f * ld + c];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int nf = (nbfc >> (2 * f)) & 3;
+                Io[f] = (code[f] >= 0) ? __ldg(kx + (size_t)code[f] * KX_COUNT + KX_I0 + nf) : R(0);
+            }
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                gn[f][0] = M.geo[(G_N0X + 3 * f) * ld + c];
+                gn[f][1] = M.geo[(G_N0Y + 3 * f) * ld + c];
+                gn[f][2] = M.geo[(G_N0L + 3 * f) * ld + c];
+            }
+            kap = M.geo[G_KAPPA * ld + c];
+        }
+        R k8[KX_COUNT];
+        load_kx<R>(kx, c, k8);
+        R vx, vy;
+        if (EQ == EULER) {
+            const R r = k8[KX_M0], mx = k8[KX_M1], my = k8[KX_M2], E = k8[KX_M3];
+            const R q = R(2) * E * r - (mx * mx + my * my);
+            bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
+            if (!ok && !(q != q)) {
+                const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
+                ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
+            }
+            if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
+            vx = mx;
+            vy = my;
+        } else {
+            vx = vy = k8[KX_M0];
+            if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+        }
+        if (all) {
+            flag = 1;
+        } else {
+            const Tab<R, K> &T = ltab<R, K>();
+            R num = R(0), lsum = R(0);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const R nx = gn[f][0], ny = gn[f][1];
+                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
+                if (!(vn < R(0))) continue;
+                const R nl = gn[f][2];
+                R J;
+                if (code[f] >= 0) {
+                    J = k8[KX_I0 + f] - Io[f];
+                } else {
+                    const BFace bf = M.bf[-code[f] - 1];
+                    const int kind = M.bc->kind[bf.tag];
+                    if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
+                        R go = R(0);
+                        for (int g = 0; g < QF; ++g) go += T.fw[g] * ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), R(0));
+                        J = k8[KX_I0 + f] - go;
+                    } else {
+                        J = R(0);  // transmissive and wall: the ghost indicator is the interior trace
+                    }
+                }
+                num += nl * J;
+                lsum += nl;
+            }
+            const R nrm2 = k8[KX_NRM2];
+            if (lsum > R(0)) {
+                const R denr = lsum * kap;
+                const R lhs = num * num, rhs = ck2 * denr * denr * nrm2;
+                if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) {
+                    flag = lhs > rhs;
+                } else {
+                    const double den = (double)lsum * (double)kap;
+                    flag = (double)num * (double)num > ck * ck * den * den * (double)nrm2;
+                }
+            }
+        }
+        flags[c] = (uint8_t)flag;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
+    }
+}
+
+template <typename R>
+void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *kx, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
+                      int32_t *flist, cudaStream_t st)
+{
+    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    const R ck2 = (R)(ck * ck);
+#define CSW_DK(E, KK) k_detect_kx<E, KK, R><<<grd, blk, 0, st>>>(M, kx, ctl, tfac, ck, ck2, all, flags, flist)
+    if (eq == BURGERS && k == 1) CSW_DK(BURGERS, 1);
+    else if (eq == BURGERS && k == 2) CSW_DK(BURGERS, 2);
+    else if (eq == EULER && k == 1) CSW_DK(EULER, 1);
+    else CSW_DK(EULER, 2);
+#undef CSW_DK
+}
+template void launch_detect_kx<float>(int, int, const MeshDev<float> &, const float *, Ctl *, double, double, int, uint8_t *,
+                                      int32_t *, cudaStream_t);
+template void launch_detect_kx<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
+                                       int32_t *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Asynchronous bulk copies global -> shared memory completed on an mbarrier
+// (cp.async.bulk, mbarrier.*: PTX ISA 8.0+, sm_90+).  Waits are bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// order this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    uint64_t g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// wait for the phase with the given parity, at most `limit` polls (each poll
+// may itself suspend for a hardware-defined time); true when it completed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int limit)
+{
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
 // CSWENO reconstruction of the flagged cells flist[0 .. nflag) into
 // lim_out[idx], from the unlimited state u.  Euler: eight lanes per cell (four
 // cells per warp), contributions summed with shuffles; Burgers: one lane per
 // cell.  The flagged cells are spread over the whole grid (a grid-stride loop
 // over the compacted list), so cells clustered along a shock do not queue up
 // in a few warps.
-template <int EQ, int K, typename R>
+template <int EQ, int K, typename R, typename W>
 __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
                                                const int32_t *__restrict__ flist, const Ctl *__restrict__ ctl, double tfac,
                                                R *__restrict__ lim_out)
@@ -970,10 +1151,10 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
         const int c = active ? flist[idx] : 0;
         if (active) {
             if (EQ == EULER)
-                limit_cell_euler_lane<K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, lane & 7,
+                limit_cell_euler_lane<K, R, W>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, lane & 7,
                                             *reinterpret_cast<R(*)[4][NP - 1]>(&res));
             else
-                limit_cell<EQ, K, R>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
+                limit_cell<EQ, K, R, W>(M, u, ops + (size_t)c * Ops<K>::SIZE, c, tl, res);
         }
         if (EQ == EULER) {
 #pragma unroll
@@ -1005,38 +1186,140 @@ __global__ void __launch_bounds__(128) k_limit(MeshDev<R> M, const R *__restrict
     }
 }
 
-template <typename R>
-void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl, double tfac,
-                  R *lim_out, int grid, cudaStream_t st)
+// Euler reconstruction with the operator blocks staged in shared memory: each
+// warp handles four flagged cells per pass (eight lanes per cell, as in
+// k_limit); lane 0 copies the four blocks (SIZE words each, contiguous in HBM)
+// with one cp.async.bulk per cell on the warp's mbarrier, so the ~430 operator
+// words a lane reads come from shared memory instead of as many dependent
+// global loads.  A copy that does not complete within the poll limit sets
+// ERR_TIMEOUT and the warp returns after a second bounded wait.
+template <int K, typename R, typename W>
+__global__ void __launch_bounds__(128) k_limit_euler_staged(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
+                                                            const int32_t *__restrict__ flist, Ctl *ctl, double tfac,
+                                                            R *__restrict__ lim_out)
+{
+    constexpr int NP = Deg<K>::NP, NV = 4, SZ = Ops<K>::SIZE, G = 8, CPW = 32 / G;
+    constexpr int POLLS = 1 << 22;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    if (!ctl->active) return;
+    const int n = ctl->nflag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    R *sop = reinterpret_cast<R *>(dsm) + (size_t)warp * CPW * SZ;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(dsm + (size_t)(blockDim.x >> 5) * CPW * SZ * sizeof(R)) + warp;
+    const int warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const int stride = gridDim.x * blockDim.x;
+    if (warp0 / G >= n) return;  // no cell for this warp (uniform)
+    const double tl = stage_time(ctl, tfac);
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    unsigned parity = 0;
+    for (int base = warp0; base / G < n; base += stride) {  // trip count uniform across the warp
+        const int idx = (base + lane) / G;
+        const bool active = idx < n;
+        const int c = active ? flist[idx] : 0;
+        const int ncell = min(CPW, n - base / G);
+        int cj[CPW];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) cj[j] = __shfl_sync(0xffffffffu, c, j * G);
+        if (lane == 0) {
+            fence_proxy_async_smem();  // the previous pass's reads of sop came before these writes
+            mbar_arrive_expect_tx(bar, (unsigned)(ncell * SZ * sizeof(R)));
+            for (int j = 0; j < ncell; ++j)
+                bulk_copy_g2s(sop + j * SZ, ops + (size_t)cj[j] * SZ, (unsigned)(SZ * sizeof(R)), bar);
+        }
+        const bool done = mbar_wait_bounded(bar, parity, POLLS);
+        if (!__all_sync(0xffffffffu, done)) {
+            if (lane == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+            mbar_wait_bounded(bar, parity, POLLS);  // let the copies in flight land before the block exits
+            return;
+        }
+        parity ^= 1u;
+        R res[NV][NP - 1];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+        if (active) limit_cell_euler_lane<K, R, W>(M, u, sop + (lane / G) * SZ, c, tl, lane & 7, res);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int i = 0; i < NP - 1; ++i) {
+                R x = res[v][i];
+                x += __shfl_xor_sync(0xffffffffu, x, 1);
+                x += __shfl_xor_sync(0xffffffffu, x, 2);
+                x += __shfl_xor_sync(0xffffffffu, x, 4);
+                res[v][i] = x;
+            }
+        bool bad = false;
+        if (active) {
+            R m0[4];
+            for (int v = 0; v < NV; ++v) m0[v] = u[sidx(NV, NP, v, 0, c)];
+            bad = positivity_bad_lane<K, R>(m0, res, lane & 7, M.gamma);
+        }
+        const unsigned grp = (__ballot_sync(0xffffffffu, bad) >> (lane & ~7)) & 0xffu;
+        if (active && (lane & 7) == 0)
+            for (int v = 0; v < NV; ++v)
+                for (int i = 0; i < NP - 1; ++i) lim_out[((size_t)idx * NV + v) * (NP - 1) + i] = grp ? R(0) : res[v][i];
+        __syncwarp();  // every lane is done with sop before lane 0 refills it
+    }
+}
+
+template <int K, typename R> size_t staged_smem_bytes(int blk) { return (size_t)(blk / 32) * 4 * Ops<K>::SIZE * sizeof(R) + (blk / 32) * 8; }
+
+template <typename R, typename W>
+void launch_limit_w(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl, double tfac,
+                    R *lim_out, int grid, cudaStream_t st)
 {
     const int blk = 128;
-    if (eq == BURGERS && k == 1) k_limit<BURGERS, 1, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
-    else if (eq == BURGERS && k == 2) k_limit<BURGERS, 2, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
-    else if (eq == EULER && k == 1) k_limit<EULER, 1, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
-    else k_limit<EULER, 2, R><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    if (eq == BURGERS && k == 1) k_limit<BURGERS, 1, R, W><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    else if (eq == BURGERS && k == 2) k_limit<BURGERS, 2, R, W><<<grid, blk, 0, st>>>(M, u, ops, flist, ctl, tfac, lim_out);
+    else if (eq == EULER && k == 1) {
+        const size_t sm = staged_smem_bytes<1, R>(blk);
+        k_limit_euler_staged<1, R, W><<<grid, blk, sm, st>>>(M, u, ops, flist, const_cast<Ctl *>(ctl), tfac, lim_out);
+    } else {
+        const size_t sm = staged_smem_bytes<2, R>(blk);
+        static bool attr_set = false;  // FP64 P2 needs more than the default 48 KB
+        if (!attr_set && sm > 48 * 1024) {
+            cudaFuncSetAttribute(k_limit_euler_staged<2, R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            attr_set = true;
+        }
+        k_limit_euler_staged<2, R, W><<<grid, blk, sm, st>>>(M, u, ops, flist, const_cast<Ctl *>(ctl), tfac, lim_out);
+    }
 }
-template void launch_limit<float>(int, int, const MeshDev<float> &, const float *, const float *, const int32_t *, const Ctl *, double,
-                                  float *, int, cudaStream_t);
-template void launch_limit<double>(int, int, const MeshDev<double> &, const double *, const double *, const int32_t *, const Ctl *,
-                                   double, double *, int, cudaStream_t);
 
 template <typename R>
-__global__ void k_scatter(int nv, int np, int ld, const int32_t *__restrict__ flist, const R *__restrict__ lim_out, R *__restrict__ u,
+void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl, double tfac,
+                  R *lim_out, int grid, int w32, cudaStream_t st)
+{
+    // smoothness indicators and weights in double unless the FP32 mode asks for float
+    if (sizeof(R) == 4 && w32) launch_limit_w<R, float>(eq, k, M, u, ops, flist, ctl, tfac, lim_out, grid, st);
+    else launch_limit_w<R, double>(eq, k, M, u, ops, flist, ctl, tfac, lim_out, grid, st);
+}
+template void launch_limit<float>(int, int, const MeshDev<float> &, const float *, const float *, const int32_t *, const Ctl *, double,
+                                  float *, int, int, cudaStream_t);
+template void launch_limit<double>(int, int, const MeshDev<double> &, const double *, const double *, const int32_t *, const Ctl *,
+                                   double, double *, int, int, cudaStream_t);
+
+// write the reconstructed modes 1..np-1 of the flagged cells back into u: one
+// thread per (cell, coefficient), so the reads of lim_out are coalesced
+template <typename R>
+__global__ void k_scatter(int nv, int np, const int32_t *__restrict__ flist, const R *__restrict__ lim_out, R *__restrict__ u,
                           const Ctl *__restrict__ ctl)
 {
     if (!ctl->active) return;
-    const int n = ctl->nflag;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
-        const int c = flist[idx];
-        for (int v = 0; v < nv; ++v)
-            for (int i = 1; i < np; ++i) u[sidx(nv, np, v, i, c)] = lim_out[((size_t)idx * nv + v) * (np - 1) + i - 1];
+    const int per = nv * (np - 1);
+    const long long total = (long long)ctl->nflag * per;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+        const int idx = (int)(t / per), r = (int)(t % per);
+        u[sidx(nv, np, r / (np - 1), r % (np - 1) + 1, flist[idx])] = lim_out[t];
     }
 }
 
 template <typename R>
 void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st)
 {
-    k_scatter<R><<<grid, 256, 0, st>>>(nv, np, ld, flist, lim_out, u, ctl);
+    (void)ld;
+    k_scatter<R><<<grid, 256, 0, st>>>(nv, np, flist, lim_out, u, ctl);
 }
 template void launch_scatter<float>(int, int, int, const int32_t *, const float *, float *, const Ctl *, int, cudaStream_t);
 template void launch_scatter<double>(int, int, int, const int32_t *, const double *, double *, const Ctl *, int, cudaStream_t);

@@ -46,22 +46,49 @@ cudaError_t operator_upload_tables()
 }
 
 // ---------------------------------------------------------------------------
+// Largest wave speed of a cell mean (given as the four mean coefficients of
+// psi_0 = sqrt(2)), in the state precision: sqrt(2)|u| (Burgers), |v| + c
+// (Euler).  A NaN state gives 1e30, which forces a tiny step; the positivity
+// check flags it.
+template <int EQ, typename R> __device__ __forceinline__ R mean_wave_speed(const R *m0, R gam)
+{
+    const R is2 = R(0.70710678118654752440);
+    if (EQ == BURGERS) return R(1.4142135623730951) * rabs(m0[0] * is2);
+    const R r = m0[0] * is2, mx = m0[1] * is2, my = m0[2] * is2, E = m0[3] * is2;
+    const R uu = mx / r, vv = my / r;
+    const R p = (gam - R(1)) * (E - R(0.5) * (mx * uu + my * vv));
+    const R lam = rsqrt_(uu * uu + vv * vv) + rsqrt_(gam * p / r);
+    return (lam >= R(0)) ? lam : R(1e30);
+}
+
+// block-wide maximum of a non-negative value folded into ctl->lam_bits (the
+// bits of a non-negative double order like the values); every thread of the
+// block must call it
+template <typename R> __device__ __forceinline__ void block_max_to_ctl(R lam, Ctl *ctl)
+{
+    for (int o = 16; o > 0; o >>= 1) lam = rmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
+    __shared__ R sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = lam;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        R m = sm[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = rmax(m, sm[i]);
+        atomicMax(&ctl->lam_bits, (unsigned long long)__double_as_longlong((double)m));
+    }
+}
+
 // Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
 // One thread per cell; each cell evaluates its volume integral and all three
 // face integrals (the neighbour's trace is read from its modes), so no face
 // buffer, colouring or atomics are needed.
 // ---------------------------------------------------------------------------
+// one cell of the stage; returns the largest wave speed of its new mean when
+// lam_next is set (else 0)
 template <int EQ, int K, typename R>
-__global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
-    k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl, double tfac, Ctl *__restrict__ ctl)
+__device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl,
+                                        double tfac, int lam_next, R *__restrict__ kx, const Ctl *__restrict__ ctl, int c)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
-    if (!ctl->active) return;
-    // the detection that follows this stage counts its flagged cells from zero
-    // (a step beyond t_end keeps the count of the last active pass)
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nflag = 0;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= M.nc) return;
     const Tab<R, K> &T = tab<R, K>();
     const int ld = M.ldc;
     const R gam = M.gammar;
@@ -97,7 +124,9 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
 
     // face integrals: -|n~| sum_g w_g psi_i F*(u-, u+; n), n the outward unit normal
     const unsigned nbf = M.nbf[c];
-#pragma unroll
+    // faces and their Gauss points are not unrolled: the fully unrolled body
+    // ran slower (instruction-cache misses and register pressure)
+#pragma unroll 1
     for (int f = 0; f < 3; ++f) {
         const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c], nl = M.geo[(G_N0L + 3 * f) * ld + c];
         const int code = M.nbr[f * ld + c];
@@ -108,7 +137,7 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
         BFace bf;
         if (code >= 0) load_cell<NV, NP>(up, code, w);
         else bf = M.bf[-code - 1];
-#pragma unroll
+#pragma unroll 1
         for (int g = 0; g < QF; ++g) {
             R Ui[NV], Uo[NV], F[NV];
 #pragma unroll
@@ -165,30 +194,85 @@ __global__ void __launch_bounds__(128, (sizeof(R) == 4) ? 4 : 1)
 #pragma unroll
             for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m];
     }
-    store_cell<NV, NP>(out, c, res);
+    {
+        store_cell<NV, NP>(out, c, res);
+        // KXRCF precursors of the new state for the detection that follows
+        if (kx) {
+            R k8[KX_COUNT];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                R s = R(0);
+#pragma unroll
+                for (int m = 0; m < NP; ++m) s += res[0][m] * T.fint[f][m];
+                k8[KX_I0 + f] = s;
+            }
+            R n2 = R(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
+            k8[KX_NRM2] = n2;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) k8[KX_M0 + v] = R(0);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) k8[KX_M0 + v] = res[v][0];
+            store_kx<R>(kx, c, k8);
+        }
+    }
+    // last stage of a step: the largest wave speed of the new means, for the next
+    // step's CFL rule (the reconstruction that follows keeps every cell mean)
+    if (!lam_next) return R(0);
+    R m0[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) m0[v] = res[v][0];
+    return mean_wave_speed<EQ, R>(m0, gam);
+}
+
+// Stage kernel: tiles of BLK consecutive cells (Morton order), one thread per
+// cell; a block takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (the grid
+// is either one block per tile or a persistent grid sized to the SMs, chosen by
+// cswdg_autotune).
+template <int EQ, int K, typename R, int BLK>
+__global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
+    k_stage(MeshDev<R> M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl, double tfac, int lam_next,
+            R *__restrict__ kx, Ctl *__restrict__ ctl)
+{
+    if (!ctl->active) return;
+    // the detection that follows this stage counts its flagged cells from zero
+    // (a step beyond t_end keeps the count of the last active pass)
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nflag = 0;
+    const int ntiles = (M.nc + BLK - 1) / BLK;
+    R lam = R(0);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int c = tile * BLK + threadIdx.x;
+        if (c < M.nc) lam = rmax(lam, stage_cell<EQ, K, R>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl, c));
+    }
+    if (lam_next) block_max_to_ctl<R>(lam, ctl);  // every thread of the block gets here
 }
 
 template <int EQ, int K, typename R>
-void launch_stage_t(const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac, Ctl *ctl,
-                    cudaStream_t st)
+void launch_stage_t(const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac, int lam_next, R *kx,
+                    Ctl *ctl, StageShape sh, cudaStream_t st)
 {
-    const int blk = 128, grd = (M.nc + blk - 1) / blk;
-    k_stage<EQ, K, R><<<grd, blk, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, ctl);
+    const int blk = (sh.blk == 64 || sh.blk == 256) ? sh.blk : 128;
+    const int ntiles = (M.nc + blk - 1) / blk;
+    const int grd = (sh.grid > 0 && sh.grid < ntiles) ? sh.grid : ntiles;
+    if (blk == 64) k_stage<EQ, K, R, 64><<<grd, 64, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
+    else if (blk == 256) k_stage<EQ, K, R, 256><<<grd, 256, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
+    else k_stage<EQ, K, R, 128><<<grd, 128, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
 }
 
 template <typename R>
 void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
-                  Ctl *ctl, cudaStream_t st)
+                  int lam_next, R *kx, Ctl *ctl, StageShape sh, cudaStream_t st)
 {
-    if (eq == BURGERS && k == 1) launch_stage_t<BURGERS, 1, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
-    else if (eq == BURGERS && k == 2) launch_stage_t<BURGERS, 2, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
-    else if (eq == EULER && k == 1) launch_stage_t<EULER, 1, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
-    else launch_stage_t<EULER, 2, R>(M, un, up, out, ca, cb, cl, tfac, ctl, st);
+    if (eq == BURGERS && k == 1) launch_stage_t<BURGERS, 1, R>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl, sh, st);
+    else if (eq == BURGERS && k == 2) launch_stage_t<BURGERS, 2, R>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl, sh, st);
+    else if (eq == EULER && k == 1) launch_stage_t<EULER, 1, R>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl, sh, st);
+    else launch_stage_t<EULER, 2, R>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl, sh, st);
 }
 template void launch_stage<float>(int, int, const MeshDev<float> &, const float *, const float *, float *, float, float, float,
-                                  double, Ctl *, cudaStream_t);
+                                  double, int, float *, Ctl *, StageShape, cudaStream_t);
 template void launch_stage<double>(int, int, const MeshDev<double> &, const double *, const double *, double *, double, double,
-                                   double, double, Ctl *, cudaStream_t);
+                                   double, double, int, double *, Ctl *, StageShape, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Time step control.  Max wave speed of the cell means (exact max, order free),
@@ -202,27 +286,12 @@ __global__ void __launch_bounds__(256) k_cfl_max(MeshDev<R> M, int np, const R *
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     R lam = R(0);
     if (c < M.nc) {
-        const R is2 = R(0.70710678118654752440);
-        if (EQ == BURGERS) {
-            lam = R(1.4142135623730951) * rabs(u[sidx(1, np, 0, 0, c)] * is2);
-        } else {
-            const R r = u[sidx(4, np, 0, 0, c)] * is2, mx = u[sidx(4, np, 1, 0, c)] * is2;
-            const R my = u[sidx(4, np, 2, 0, c)] * is2, E = u[sidx(4, np, 3, 0, c)] * is2;
-            const R uu = mx / r, vv = my / r;
-            const R p = ((R)M.gamma - R(1)) * (E - R(0.5) * (mx * uu + my * vv));
-            lam = rsqrt_(uu * uu + vv * vv) + rsqrt_((R)M.gamma * p / r);
-            if (!(lam >= R(0))) lam = R(1e30);  // NaN state: force a tiny step, flagged by the positivity check
-        }
+        R m0[4];
+        const int nv = (EQ == BURGERS) ? 1 : 4;
+        for (int v = 0; v < nv; ++v) m0[v] = u[sidx(nv, np, v, 0, c)];
+        lam = mean_wave_speed<EQ, R>(m0, M.gammar);
     }
-    for (int o = 16; o > 0; o >>= 1) lam = rmax(lam, __shfl_xor_sync(0xffffffffu, lam, o));
-    __shared__ R sm[8];
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = lam;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        R m = sm[0];
-        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = rmax(m, sm[i]);
-        atomicMax(&ctl->lam_bits, (unsigned long long)__double_as_longlong((double)m));
-    }
+    block_max_to_ctl<R>(lam, ctl);
 }
 
 // begin a step: t <- t_next, choose dt (fixed or CFL), clip to t_end
@@ -241,7 +310,9 @@ __global__ void k_begin_step(Ctl *ctl, int use_cfl)
     ctl->dtf = (float)dt;
     ctl->active = dt > 0.0;
     ctl->t_next = ctl->t + dt;
-    ctl->lam_bits = 0ull;
+    // the last stage of an active step folds the next maximum into lam_bits; an
+    // inactive step leaves the state, and so its maximum, unchanged
+    if (dt > 0.0) ctl->lam_bits = 0ull;
 }
 
 template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st)

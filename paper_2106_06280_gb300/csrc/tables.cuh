@@ -61,6 +61,12 @@ template <typename R, int K> inline void make_tab(Tab<R, K> &T)
                 T.fphi[f][g][m] = (R)v;
             }
         }
+    for (int f = 0; f < 3; ++f)
+        for (int m = 0; m < NP; ++m) {
+            double acc = 0.0;
+            for (int g = 0; g < QF; ++g) acc += w[g] * (double)T.fphi[f][g][m];
+            T.fint[f][m] = (R)acc;
+        }
 }
 
 }  // namespace csw

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcswdg.so")
 OK, EINVAL, ECUDA, EMESH, ENONPHYS, ELSQ, ETIMEOUT, ENOMEM = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ECUDA", "EMESH", "ENONPHYS", "ELSQ", "ETIMEOUT", "ENOMEM"]
 BURGERS, EULER = 0, 1
-FP64, FP32_BULK = 0, 1
+FP64, FP32_BULK, FP32 = 0, 1, 2
 LIMITER_OFF, LIMITER_KXRCF, LIMITER_ALL = 0, 1, 2
 
 
@@ -65,6 +65,8 @@ def _load():
         "cswdg_internal_layout": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
         "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
         "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
+        "cswdg_autotune": ([vp, dp, C.POINTER(i32)], C.c_int),
+        "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -79,7 +81,9 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_launches_per_step", "cswdg_get_time",
             "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
-            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc"]
+            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_autotune",
+            "cswdg_set_stage_shape"]
+TUNE_CANDIDATES = 7
 
 
 def _d(a):
@@ -92,7 +96,7 @@ def _p(a, ctype=C.c_double):
 
 class Solver:
     """One solver handle.  equation: BURGERS/EULER, degree 1/2, precision
-    FP64/FP32_BULK, limiter LIMITER_*; stream: a cudaStream_t as int (e.g.
+    FP64/FP32_BULK/FP32, limiter LIMITER_*; stream: a cudaStream_t as int (e.g.
     torch.cuda.current_stream().cuda_stream) or None."""
 
     def __init__(self, equation, degree, precision=FP64, limiter=LIMITER_KXRCF, c_k=1.0, cfl=0.1,
@@ -165,6 +169,17 @@ class Solver:
         nl = C.c_int64()
         self._chk(lib.cswdg_profile_step(self.h, dt, nsteps, t_end, _p(ms), C.byref(nl)))
         return dict(cfl=ms[0], stage=ms[1], detect=ms[2], limit=ms[3], scatter=ms[4]), int(nl.value)
+
+    def autotune(self):
+        """Pick the stage kernel's launch shape on the current state; returns
+        (cells per block, grid or 0, per-candidate ms)."""
+        ms = np.zeros(TUNE_CANDIDATES)
+        ch = np.zeros(2, dtype=np.int32)
+        self._chk(lib.cswdg_autotune(self.h, _p(ms), ch.ctypes.data_as(C.POINTER(C.c_int32))))
+        return int(ch[0]), int(ch[1]), ms
+
+    def set_stage_shape(self, cells_per_block, grid=0):
+        self._chk(lib.cswdg_set_stage_shape(self.h, cells_per_block, grid))
 
     def launches_per_step(self, use_cfl=True):
         return int(lib.cswdg_launches_per_step(self.h, int(use_cfl)))

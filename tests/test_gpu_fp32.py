@@ -1,6 +1,8 @@
-"""GPU parity in FP32-bulk mode, the precision the benchmark runs in: double
-Mach reflection, Euler P2, 960x240 (460,800 cells), in the launch
-configuration of the benchmark, against the FP64 oracle on 600 sampled cells.
+"""GPU parity in the two float modes -- FP32-bulk (the benchmark's precision:
+float state and operator, double smoothness indicators and weights) and FP32
+(those in float as well) -- on the double Mach reflection, Euler P2, 960x240
+(460,800 cells), in the launch configuration of the benchmark, against the
+FP64 oracle on 600 sampled cells.
 
 Inputs: a seeded random admissible state and the projected discontinuous
 initial condition (for the operator, which needs positive pressure at its
@@ -84,11 +86,12 @@ def test_fp32_operator_sampled(csw, cuda_stream, dmr):
     s.close()
 
 
-def test_fp32_reconstruction_all_cells_sampled(csw, cuda_stream, dmr):
+@pytest.mark.parametrize("mode", ["FP32_BULK", "FP32"])
+def test_fp32_reconstruction_all_cells_sampled(csw, cuda_stream, dmr, mode):
     """Every cell reconstructed (the initial-condition pass): the FP32 smoothness
     indicators, nonlinear weights and characteristic projections."""
     pb, o, cells = dmr
-    s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_ALL, stream=cuda_stream)
+    s = csw.Solver(1, 2, getattr(csw, mode), csw.LIMITER_ALL, stream=cuda_stream)
     s.setup(pb)
     for name, u in states(pb, o):
         ug, fg = s.limit(u, 0.0)
@@ -100,11 +103,12 @@ def test_fp32_reconstruction_all_cells_sampled(csw, cuda_stream, dmr):
     s.close()
 
 
-def test_fp32_kxrcf_flags_and_reconstruction_sampled(csw, cuda_stream, dmr):
+@pytest.mark.parametrize("mode", ["FP32_BULK", "FP32"])
+def test_fp32_kxrcf_flags_and_reconstruction_sampled(csw, cuda_stream, dmr, mode):
     """The projected initial condition: flags on every cell, reconstruction on a
     sample of 300 flagged cells (the shock and the wall corner)."""
     pb, o, _ = dmr
-    s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s = csw.Solver(1, 2, getattr(csw, mode), csw.LIMITER_KXRCF, stream=cuda_stream)
     s.setup(pb)
     u = to_f32(o.project(pb.u0))
     ug, fg = s.limit(u, 0.0)

@@ -146,3 +146,48 @@ def test_project_ic_all_cells_limited(csw, cuda_stream):
     uo, fo, st = oa.limit(oa.project(pb.u0), 0.0)
     for v in range(pb.nvar):
         assert rel(ug[:, v], uo[:, v]) < TOL64
+
+
+@pytest.mark.parametrize("shape", [(64, 0), (128, 0), (256, 0), (64, 3), (128, 2), (256, 1)])
+def test_stage_shapes_fp64(csw, cuda_stream, shape):
+    """Every launch shape of the stage kernel (tiles of 64/128/256 cells, one
+    block per tile or a small persistent grid looping over several tiles) gives
+    the oracle's operator (DMR boundaries, random state) and its CFL steps (the
+    wave-speed maximum of the next step is folded into the last stage), on a
+    338-cell periodic Euler mesh: 2 to 6 tiles per launch, ragged last tile."""
+    pb = problems()["dmr"]
+    s, o = make(csw, cuda_stream, pb, 2, 1)
+    s.set_stage_shape(*shape)
+    u = random_state(pb, 2, 500)
+    assert rel(s.eval_rhs(u, 0.011), o.rhs(u, 0.011)) < TOL64
+    s.close()
+    pb = W.euler_entropy_wave(13, seed=41)
+    s, o = make(csw, cuda_stream, pb, 2, 1)
+    s.set_stage_shape(*shape)
+    u = o.project(pb.u0)
+    s.write_modes(u)
+    s.set_time(0.0)
+    t, uo = 0.0, u
+    for n in range(3):
+        dt = o.cfl_dt(uo, 0.1)
+        uo, _, st = o.step(uo, t, dt)
+        assert st == 0
+        t += dt
+    tg = s.step(0.0, 3, 1e9)
+    assert abs(tg - t) < 1e-13 * t
+    assert rel(s.read_modes(), uo) < TOL64
+
+
+def test_autotune_keeps_results(csw, cuda_stream):
+    pb = problems()["riemann"]
+    s, o = make(csw, cuda_stream, pb, 2, 1)
+    u = random_state(pb, 2, 501)
+    s.write_modes(u)
+    blk, grid, ms = s.autotune()
+    assert blk in (64, 128, 256) and grid >= 0 and np.all(ms > 0)
+    assert np.allclose(s.read_modes(), u, rtol=0, atol=1e-15 * np.abs(u).max())  # state untouched
+    s.set_time(0.0)
+    dt = 0.5 * o.cfl_dt(u, 0.1)
+    uo, _, _ = o.step(u, 0.0, dt)
+    s.step(dt, 1, 1e9)
+    assert rel(s.read_modes(), uo) < TOL64
