@@ -117,8 +117,10 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
         for (int v = 0; v < NV; ++v) {
             const R Fr = T.vw[q] * (g0 * f[v] + g1 * g[v]);
             const R Fs = T.vw[q] * (g2 * f[v] + g3 * g[v]);
+            // psi_0 is constant and psi_1..psi_K (Jacobi index i = 0) do not depend on r:
+            // their derivative terms are exact zeros and are skipped
 #pragma unroll
-            for (int m = 0; m < NP; ++m) acc[v][m] += T.vdr[q][m] * Fr + T.vds[q][m] * Fs;
+            for (int m = 1; m < NP; ++m) acc[v][m] += (m > K) ? T.vdr[q][m] * Fr + T.vds[q][m] * Fs : T.vds[q][m] * Fs;
         }
     }
 
