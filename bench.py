@@ -260,6 +260,37 @@ def run_ours(args):
         return {"value": float(nc) * NP * NV * 3 * nsteps / (ms2 * 1e-3), "unit": UNIT,
                 "ms_per_step": ms2 / nsteps, "steps": nsteps, "precision": what}
 
+    def adjoint(nsteps):
+        """Hand-written adjoint on the isentropic-vortex workload (periodic
+        [0,10]^2, 300x300 split squares = 180,000 triangles, Euler P2,
+        FP32-bulk): nsteps fixed-dt steps forward with checkpoints every 20,
+        then the reverse sweep, through cswdg_adjoint_steps from host buffers."""
+        if nsteps <= 0:
+            return None
+        pbv = W.isentropic_vortex(300, seed=5, box=(0.0, 10.0, 0.0, 10.0))
+        sv = csw.Solver(csw.EULER, K, csw.FP32_BULK, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=stream)
+        sv.setup(pbv)
+        sv.project_ic(pbv.u0, apply_limiter=1)
+        u0v = sv.read_modes()
+        dtv = 0.5 * sv.cfl_dt()
+        gTv = np.zeros_like(u0v)
+        gTv[:, 0, :] = 2.0 * u0v[:, 0, :]
+        sv.set_time(0.0)
+        sv.adjoint_steps(u0v, gTv, dtv, 2, 20)  # warm-up (graph capture, allocations)
+        sv.set_time(0.0)
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        sv.adjoint_steps(u0v, gTv, dtv, nsteps, 20)
+        tb = time.perf_counter()
+        ncv = pbv.mesh.nc
+        sv.close()
+        return {"workload": "isentropic vortex, periodic [0,10]^2, 180,000 triangles, Euler P2, FP32-bulk, fixed dt",
+                "steps": nsteps, "checkpoint_every": 20, "seconds": tb - ta,
+                "value": float(ncv) * NP * NV * 3 * nsteps / (tb - ta), "unit": UNIT,
+                "note": "forward with checkpoints + recomputation + reverse sweep, host buffers in and out; "
+                        "value counts the forward DOF-stage updates once"}
+
+    adj = adjoint(args.adjoint_steps)
     fp32 = secondary(csw.FP32, args.fp32_steps, "FP32 mode: smoothness indicators and nonlinear weights in float as well "
                                                  "(quotient forms), FP64 only for close calls of the decisions")
     fp64 = secondary(csw.FP64, args.fp64_steps, "FP64 mode: every step in double")
@@ -291,6 +322,7 @@ def run_ours(args):
                 "path": "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)"},
         "gpu_launches": launches,
         "clocks": clk,
+        "adjoint": adj,
         "fp32_weights": fp32,
         "fp64": fp64,
     }
@@ -369,6 +401,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp32-steps", type=int, default=10)
+    ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--stage-shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     help="cells per block and grid of the stage kernel (e.g. 256,304); default: autotune")
     ap.add_argument("--cpu-sample", type=int, default=200000)

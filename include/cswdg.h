@@ -143,6 +143,48 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
 cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end,
                                 double *ms_host, int64_t *launches_host);
 
+/* Adjoint of the spatial operator (Sec. 2 weak form with the quadrature,
+ * local Lax-Friedrichs flux and boundary ghosts of cswdg_eval_rhs):
+ * grad = (dL_h/du)^T lambda at state modes_in and time t, all host arrays of
+ * nc*nvar*np doubles in the user basis and cell order (as cswdg_eval_rhs), so
+ * that  sum(lambda * (L_h(u + e d) - L_h(u)))/e -> sum(grad * d).  At the
+ * maximum inside the Lax-Friedrichs speed the derivative follows the branch the
+ * forward flux takes.  The limiter is not part of L_h.  Overwrites the
+ * solver's state (as cswdg_eval_rhs).  Errors: EINVAL, ECUDA. */
+cswdg_status cswdg_rhs_adjoint(cswdg_solver *s, double t, const double *modes_in, const double *lambda_in, double *grad_out);
+
+/* Adjoint of one limiter pass (Sec. 3.1 detection, Sec. 3.2 reconstruction)
+ * at state modes_in and time t, with the troubled-cell flags frozen as the
+ * forward pass sets them: grad = (d Lim/du)^T lambda, where Lim keeps the
+ * unflagged cells and the cell means and replaces the other modes of flagged
+ * cells by the reconstruction; the derivative runs through the least-squares
+ * fits, smoothness indicators, nonlinear weights and (Euler) the
+ * characteristic transforms.  A cell whose reconstruction the positivity
+ * fallback replaced contributes nothing.  flags_out (nullable, nc bytes): the
+ * flags.  Host arrays as cswdg_rhs_adjoint.  Overwrites the solver's state.
+ * Errors: EINVAL (limiter off), ECUDA. */
+cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_in, const double *lambda_in, double *grad_out,
+                                 uint8_t *flags_out);
+
+/* Hand-written adjoint of nsteps fixed-dt SSP-RK3 steps (Sec. 4, Table tvd)
+ * with the limiter after every stage (Sec. 3): runs the steps forward from
+ * u0_user, keeping the state every checkpoint_every steps, then sweeps back:
+ * each segment is recomputed stage by stage from its checkpoint (keeping the
+ * unlimited stage outputs and the troubled-cell lists), and the transposed
+ * stage updates are applied with the operator adjoint of cswdg_rhs_adjoint
+ * and the limiter adjoint of cswdg_limit_adjoint (flags frozen as the forward
+ * run set them, derivatives through the WENO weights).  Returns in g0_user
+ * the gradient (du_N/du_0)^T gT_user, and in uT_user (nullable) the final
+ * state u_N.  dt is held fixed (the CFL choice of dt is not differentiated);
+ * the every-cell limiter is treated like KXRCF with every cell flagged.  Host
+ * arrays: nc*nvar*np doubles, user basis and cell order.  Device work
+ * memory: about (nsteps/checkpoint_every + 6 checkpoint_every + 5) state
+ * arrays and 3 checkpoint_every cell lists, allocated and freed inside the
+ * call.  Leaves the solver at u_N and t + nsteps dt.
+ * Errors: EINVAL, ENONPHYS, ENOMEM, ECUDA. */
+cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int32_t checkpoint_every, const double *u0_user,
+                                 const double *gT_user, double *uT_user, double *g0_user);
+
 /* Launch-shape autotuner for the stage kernel (operator + RK update; no
  * counterpart in the paper).  Times CSWDG_TUNE_CANDIDATES shapes -- cells per
  * block 64/128/256, one block per tile of cells or a persistent grid of

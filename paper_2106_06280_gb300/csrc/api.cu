@@ -43,6 +43,7 @@ struct cswdg_solver {
     BcTab *bcd = nullptr;
     int32_t *dperm = nullptr;
     double *sc = nullptr, *area = nullptr;
+    double *isc = nullptr;  // 1 / sc: the scaling of adjoint (dual) vectors
     void *ops = nullptr;
     uint8_t *flags = nullptr, *flags_user = nullptr;
     int32_t *flist = nullptr;
@@ -101,7 +102,7 @@ void free_device(cswdg_solver *s)
 {
     for (int i = 0; i < 2; ++i)
         if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
-    void *ptrs[] = {s->U, s->A, s->B, s->geo, s->nbr, s->nbf, s->bf, s->bcd, s->dperm, s->sc, s->area, s->ops, s->flags,
+    void *ptrs[] = {s->U, s->A, s->B, s->geo, s->nbr, s->nbf, s->bf, s->bcd, s->dperm, s->sc, s->isc, s->area, s->ops, s->flags,
                     s->flags_user, s->flist, s->lim_out, s->kx, s->ctl, s->dev_user, s->cons_part, s->cons_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -110,7 +111,7 @@ void free_device(cswdg_solver *s)
     s->nbf = s->flags = s->flags_user = nullptr;
     s->bf = nullptr;
     s->bcd = nullptr;
-    s->sc = s->area = s->dev_user = s->cons_part = s->cons_out = nullptr;
+    s->sc = s->isc = s->area = s->dev_user = s->cons_part = s->cons_out = nullptr;
     s->ctl = nullptr;
     s->mesh_ready = false;
 }
@@ -281,21 +282,26 @@ cswdg_status check_err(cswdg_solver *s, Ctl *h)
     return CSWDG_OK;
 }
 
-cswdg_status upload_modes(cswdg_solver *s, const double *modes, void *dst)
+// user modes (physically orthonormal basis, user cell order) -> internal array;
+// dual vectors (adjoint variables, gradients) pass dual = true: they scale
+// with the inverse factor so that dot products are preserved
+cswdg_status upload_modes(cswdg_solver *s, const double *modes, void *dst, bool dual = false)
 {
     const size_t n = (size_t)s->nc * s->nv * s->np;
+    const double *sc = dual ? s->isc : s->sc;
     CK(cudaMemcpyAsync(s->dev_user, modes, n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-    if (s->fp32) launch_from_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, s->dev_user, (float *)dst, s->stream);
-    else launch_from_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, s->dev_user, (double *)dst, s->stream);
+    if (s->fp32) launch_from_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, sc, s->dev_user, (float *)dst, s->stream);
+    else launch_from_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, sc, s->dev_user, (double *)dst, s->stream);
     CK(cudaGetLastError());
     return CSWDG_OK;
 }
 
-cswdg_status download_modes(cswdg_solver *s, const void *src, double *modes)
+cswdg_status download_modes(cswdg_solver *s, const void *src, double *modes, bool dual = false)
 {
     const size_t n = (size_t)s->nc * s->nv * s->np;
-    if (s->fp32) launch_to_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const float *)src, s->dev_user, s->stream);
-    else launch_to_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const double *)src, s->dev_user, s->stream);
+    const double *sc = dual ? s->isc : s->sc;
+    if (s->fp32) launch_to_user<float>(s->nc, s->ldc, s->nv, s->np, s->dperm, sc, (const float *)src, s->dev_user, s->stream);
+    else launch_to_user<double>(s->nc, s->ldc, s->nv, s->np, s->dperm, sc, (const double *)src, s->dev_user, s->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(modes, s->dev_user, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
@@ -357,6 +363,7 @@ cswdg_status cswdg_create(const cswdg_config *cfg, cswdg_solver **out)
     if (!tables_ready) {
         cudaError_t e = operator_upload_tables();
         if (e == cudaSuccess) e = limiter_upload_tables();
+        if (e == cudaSuccess) e = adjoint_upload_tables();
         if (e != cudaSuccess) {
             delete s;
             return CSWDG_ECUDA;
@@ -431,6 +438,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     A_(dalloc(&s->bcd, 1));
     A_(dalloc(&s->dperm, (size_t)ld));
     A_(dalloc(&s->sc, (size_t)ld));
+    A_(dalloc(&s->isc, (size_t)ld));
     A_(dalloc(&s->area, (size_t)ld));
     A_(dalloc(&s->flags, (size_t)ld));
     A_(dalloc(&s->flags_user, (size_t)ld));
@@ -456,6 +464,10 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     CK(cudaMemcpyAsync(s->bcd, &s->bc, sizeof(BcTab), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->dperm, s->perm.data(), (size_t)nc * 4, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(s->sc, scv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
+    std::vector<double> iscv(ld);
+    for (int i = 0; i < ld; ++i) iscv[i] = (scv[i] != 0.0) ? 1.0 / scv[i] : 0.0;
+    CK(cudaMemcpyAsync(s->isc, iscv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     CK(cudaMemcpyAsync(s->area, arv.data(), (size_t)ld * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(s->U, 0, nstate * rs, st));
     s->lam_stale = true;
@@ -854,5 +866,246 @@ cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int
     s->shape.grid = grid;
     for (int i = 0; i < 2; ++i)
         if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
+    return CSWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the operator (host buffers in the user basis and cell order)
+// ---------------------------------------------------------------------------
+cswdg_status cswdg_rhs_adjoint(cswdg_solver *s, double t, const double *modes_in, const double *lambda_in, double *grad_out)
+{
+    if (!s || !s->mesh_ready || !modes_in || !lambda_in || !grad_out) return fail(s, CSWDG_EINVAL, "rhs_adjoint");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.t = t;
+    w.dt = 1.0;
+    w.active = 1;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    s->lam_stale = true;
+    if (cswdg_status r = upload_modes(s, lambda_in, s->A, true)) return r;
+    if (s->fp32)
+        launch_rhs_adjoint<float>(s->eq, s->k, mesh_dev<float>(s), (const float *)s->U, (const float *)s->A, (float *)s->B, 0.0, s->ctl,
+                                  s->stream);
+    else
+        launch_rhs_adjoint<double>(s->eq, s->k, mesh_dev<double>(s), (const double *)s->U, (const double *)s->A, (double *)s->B, 0.0,
+                                   s->ctl, s->stream);
+    CK(cudaGetLastError());
+    if (cswdg_status r = download_modes(s, s->B, grad_out, true)) return r;
+    return write_ctl(s, &h);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of one limiter pass with the flags of the forward pass frozen
+// ---------------------------------------------------------------------------
+template <typename R>
+static void limit_adjoint_dev(cswdg_solver *s, const void *u_pre, const int32_t *flist, const int32_t *nflag_dev, double tfac,
+                              const void *gin, void *gout, size_t nstate, cudaStream_t st)
+{
+    cudaMemcpyAsync(gout, gin, nstate * sizeof(R), cudaMemcpyDeviceToDevice, st);
+    launch_limit_adjoint<R>(s->eq, s->k, mesh_dev<R>(s), (const R *)u_pre, (const R *)s->ops, flist, nflag_dev, s->ctl, tfac, s->w32,
+                            (const R *)gin, (R *)gout, s->lim_grid, st);
+}
+
+cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_in, const double *lambda_in, double *grad_out,
+                                 uint8_t *flags_out)
+{
+    if (!s || !s->mesh_ready || !modes_in || !lambda_in || !grad_out) return fail(s, CSWDG_EINVAL, "limit_adjoint");
+    if (s->cfg.limiter == CSWDG_LIMITER_OFF) return fail(s, CSWDG_EINVAL, "limit_adjoint: the limiter is off");
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    Ctl w = h;
+    w.t = t;
+    w.dt = 0.0;
+    w.active = 1;
+    w.err = 0;
+    if (cswdg_status r = write_ctl(s, &w)) return r;
+    if (cswdg_status r = upload_modes(s, modes_in, s->U)) return r;
+    s->lam_stale = true;
+    // the forward pass (its flags and reconstructions), then the reverse
+    CK(cudaMemcpyAsync(s->B, s->U, (size_t)s->nv * s->np * s->ldc * (s->fp32 ? 4 : 8), cudaMemcpyDeviceToDevice, s->stream));
+    if (cswdg_status r = limiter_pass(s, s->B, 0.0, s->stream)) return r;
+    if (cswdg_status r = upload_modes(s, lambda_in, s->A, true)) return r;
+    const size_t nstate = (size_t)s->nv * s->np * s->ldc;
+    if (s->fp32) limit_adjoint_dev<float>(s, s->U, s->flist, &s->ctl->nflag, 0.0, s->A, s->B, nstate, s->stream);
+    else limit_adjoint_dev<double>(s, s->U, s->flist, &s->ctl->nflag, 0.0, s->A, s->B, nstate, s->stream);
+    CK(cudaGetLastError());
+    if (cswdg_status r = download_modes(s, s->B, grad_out, true)) return r;
+    if (flags_out)
+        if (cswdg_status r = cswdg_read_flags(s, flags_out)) return r;
+    Ctl after;
+    if (cswdg_status r = read_ctl(s, &after)) return r;
+    h.nflag = after.nflag;
+    h.err = after.err;
+    if (cswdg_status r = write_ctl(s, &h)) return r;
+    return check_err(s, &h);
+}
+
+// ---------------------------------------------------------------------------
+// Reverse sweep of fixed-dt SSP-RK3 steps with checkpoints (hand-written
+// adjoint; see the header).  Per step, with Lam_i the limiter pass after
+// stage i (flags frozen), v1 = u0 + dt L(u0), u1 = Lam_1(v1),
+// v2 = 3/4 u0 + 1/4 (u1 + dt L(u1)), u2 = Lam_2(v2),
+// v3 = 1/3 u0 + 2/3 (u2 + dt L(u2)), u3 = Lam_3(v3):
+//   b3 = Lam_3'^T g;  w = 2/3 b3;  h2 = w + dt L'(u2)^T w;  b2 = Lam_2'^T h2
+//   g0 = 1/3 b3 + 3/4 b2;  w = 1/4 b2;  h1 = w + dt L'(u1)^T w;  b1 = Lam_1'^T h1
+//   g0 += b1 + dt L'(u0)^T b1
+// ---------------------------------------------------------------------------
+cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int32_t checkpoint_every, const double *u0_user,
+                                 const double *gT_user, double *uT_user, double *g0_user)
+{
+    if (!s || !s->mesh_ready || !(dt > 0.0) || nsteps < 1 || checkpoint_every < 1 || !u0_user || !gT_user || !g0_user)
+        return fail(s, CSWDG_EINVAL, "adjoint_steps: bad arguments");
+    const bool lim = s->cfg.limiter != CSWDG_LIMITER_OFF;
+    const size_t rs = s->fp32 ? 4 : 8, nstate = (size_t)s->nv * s->np * s->ldc, bytes = nstate * rs;
+    const size_t flbytes = (size_t)s->ldc * 4;
+    const int64_t ce = checkpoint_every, nck = (nsteps + ce - 1) / ce;
+    // per step of a segment: u^n, the three unlimited stage outputs v1..v3 and the
+    // limited u1, u2; the three flag lists and their counts
+    const int NS = 6;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = nsm * 4;
+    char *ck = nullptr, *seg = nullptr, *ga = nullptr, *gw = nullptr, *gt = nullptr, *gx = nullptr, *uN = nullptr;
+    int32_t *fls = nullptr, *nfs = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto A_ = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A_(cudaMalloc((void **)&ck, (size_t)nck * bytes));
+    A_(cudaMalloc((void **)&seg, (size_t)NS * ce * bytes));
+    A_(cudaMalloc((void **)&ga, bytes));
+    A_(cudaMalloc((void **)&gw, bytes));
+    A_(cudaMalloc((void **)&gt, bytes));
+    A_(cudaMalloc((void **)&gx, bytes));
+    A_(cudaMalloc((void **)&uN, bytes));
+    if (lim) {
+        A_(cudaMalloc((void **)&fls, (size_t)3 * ce * flbytes));
+        A_(cudaMalloc((void **)&nfs, (size_t)3 * ce * 4));
+    }
+    auto release = [&]() {
+        cudaFree(ck); cudaFree(seg); cudaFree(ga); cudaFree(gw); cudaFree(gt); cudaFree(gx); cudaFree(uN);
+        cudaFree(fls); cudaFree(nfs);
+    };
+    if (e != cudaSuccess) {
+        release();
+        return fail(s, CSWDG_ENOMEM, "adjoint_steps: device allocation: %s", cudaGetErrorString(e));
+    }
+#define CKR(x)                                                                                           \
+    do {                                                                                                 \
+        cudaError_t e_ = (x);                                                                            \
+        if (e_ != cudaSuccess) { release(); return fail(s, CSWDG_ECUDA, "%s", cudaGetErrorString(e_)); } \
+    } while (0)
+#define STR(x)                                        \
+    do {                                              \
+        cswdg_status r_ = (x);                        \
+        if (r_ != CSWDG_OK) { release(); return r_; } \
+    } while (0)
+    Ctl h;
+    STR(read_ctl(s, &h));
+    // the step times exactly as k_begin_step accumulates them
+    std::vector<double> times((size_t)nsteps + 1);
+    times[0] = h.t_next;
+    for (int64_t n = 0; n < nsteps; ++n) times[n + 1] = times[n] + dt;
+    h.dt_fixed = dt;
+    h.t_end = 1e300;
+    STR(upload_modes(s, u0_user, s->U));
+    s->lam_stale = true;
+    STR(write_ctl(s, &h));
+    STR(get_graph(s, 0));
+    // forward sweep, checkpoints of u^n every ce steps
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (n % ce == 0) CKR(cudaMemcpyAsync(ck + (size_t)(n / ce) * bytes, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CKR(cudaGraphLaunch(s->graph[0], s->stream));
+    }
+    CKR(cudaMemcpyAsync(uN, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    Ctl hf;
+    STR(read_ctl(s, &hf));
+    if (cswdg_status r = check_err(s, &hf)) { release(); return r; }
+    if (uT_user) STR(download_modes(s, s->U, uT_user));
+    // reverse sweep
+    STR(upload_modes(s, gT_user, ga, true));
+    for (int64_t sg = nck - 1; sg >= 0; --sg) {
+        const int64_t n0 = sg * ce, n1 = std::min(nsteps, n0 + ce);
+        CKR(cudaMemcpyAsync(s->U, ck + (size_t)sg * bytes, bytes, cudaMemcpyDeviceToDevice, s->stream));
+        // recompute the segment stage by stage, keeping what the reverse sweep reads
+        for (int64_t n = n0; n < n1; ++n) {
+            char *base = seg + (size_t)NS * (n - n0) * bytes;
+            int32_t *fl = lim ? fls + (size_t)3 * (n - n0) * s->ldc : nullptr;
+            int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
+            Ctl ws = hf;
+            ws.t = times[n];
+            ws.dt = dt;
+            ws.active = 1;
+            STR(write_ctl(s, &ws));
+            CKR(cudaMemcpyAsync(base, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
+            void *outs[3] = {s->A, s->B, s->U};
+            const void *ins[3] = {s->U, s->A, s->B};
+            const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0}, tf[3] = {0.0, 1.0, 0.5},
+                         tl[3] = {1.0, 0.5, 1.0};
+            for (int k = 0; k < 3; ++k) {
+                STR(stage(s, k ? s->U : nullptr, ins[k], outs[k], ca[k], cb[k], cb[k], tf[k], s->stream, nullptr, 0, lim));
+                CKR(cudaMemcpyAsync(base + (size_t)(1 + k) * bytes, outs[k], bytes, cudaMemcpyDeviceToDevice, s->stream));
+                if (lim) {
+                    STR(limiter_pass(s, outs[k], tl[k], s->stream, nullptr, false, true));
+                    CKR(cudaMemcpyAsync(fl + (size_t)k * s->ldc, s->flist, flbytes, cudaMemcpyDeviceToDevice, s->stream));
+                    CKR(cudaMemcpyAsync(nf + k, &s->ctl->nflag, 4, cudaMemcpyDeviceToDevice, s->stream));
+                }
+                if (k < 2) CKR(cudaMemcpyAsync(base + (size_t)(4 + k) * bytes, outs[k], bytes, cudaMemcpyDeviceToDevice, s->stream));
+            }
+        }
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            const char *base = seg + (size_t)NS * (n - n0) * bytes;
+            const int32_t *fl = lim ? fls + (size_t)3 * (n - n0) * s->ldc : nullptr;
+            const int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
+            Ctl ws = hf;
+            ws.t = times[n];
+            ws.dt = dt;
+            ws.active = 1;
+            STR(write_ctl(s, &ws));
+            const void *u0s = base, *v1 = base + bytes, *v2 = base + 2 * bytes, *v3 = base + 3 * bytes, *u1s = base + 4 * bytes,
+                       *u2s = base + 5 * bytes;
+            auto run = [&](auto tag) {
+                using R = decltype(tag);
+                const MeshDev<R> M = mesh_dev<R>(s);
+                const R d = (R)dt;
+                R *a = (R *)ga, *wv = (R *)gw, *tv = (R *)gt, *xv = (R *)gx;
+                if (lim) {  // b3 = Lam_3'^T g
+                    limit_adjoint_dev<R>(s, v3, fl + 2 * (size_t)s->ldc, nf + 2, 1.0, a, xv, nstate, s->stream);
+                    cudaMemcpyAsync(a, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                }
+                launch_axpby<R>(nstate, R(2) / R(3), a, R(0), nullptr, wv, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u2s, wv, tv, 0.5, s->ctl, s->stream);
+                launch_axpby<R>(nstate, R(1), wv, d, tv, tv, grid, s->stream);
+                if (lim) {  // b2 = Lam_2'^T h2
+                    limit_adjoint_dev<R>(s, v2, fl + (size_t)s->ldc, nf + 1, 0.5, tv, xv, nstate, s->stream);
+                    cudaMemcpyAsync(tv, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                }
+                launch_axpby<R>(nstate, R(1) / R(3), a, R(0.75), tv, a, grid, s->stream);
+                launch_axpby<R>(nstate, R(0.25), tv, R(0), nullptr, wv, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u1s, wv, tv, 1.0, s->ctl, s->stream);
+                launch_axpby<R>(nstate, R(1), wv, d, tv, tv, grid, s->stream);
+                if (lim) {  // b1 = Lam_1'^T h1
+                    limit_adjoint_dev<R>(s, v1, fl, nf, 1.0, tv, xv, nstate, s->stream);
+                    cudaMemcpyAsync(tv, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                }
+                launch_axpby<R>(nstate, R(1), a, R(1), tv, a, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u0s, tv, wv, 0.0, s->ctl, s->stream);
+                launch_axpby<R>(nstate, R(1), a, d, wv, a, grid, s->stream);
+            };
+            if (s->fp32) run(float(0));
+            else run(double(0));
+            CKR(cudaGetLastError());
+        }
+    }
+    STR(download_modes(s, ga, g0_user, true));
+    // leave the solver at u^N and t^N
+    CKR(cudaMemcpyAsync(s->U, uN, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    Ctl fin = hf;
+    fin.t = fin.t_next = times[nsteps];
+    STR(write_ctl(s, &fin));
+    release();
+#undef CKR
+#undef STR
     return CSWDG_OK;
 }

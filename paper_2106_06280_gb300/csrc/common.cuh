@@ -164,6 +164,7 @@ struct Ctl {
     int32_t nflag;   // flagged-cell count of the last pass
     int32_t active;  // 1: kernels run; 0: step beyond t_end, kernels return
     float dtf;       // dt rounded to float (FP32-bulk stage update)
+    long long nflag_sum;  // flagged cells summed over the limiter passes since the host last cleared it
 };
 
 // time t + tfac dt of the current stage, for boundary data.  The loads are

@@ -26,6 +26,7 @@ template <int K> struct Ops {
 
 cudaError_t operator_upload_tables();
 cudaError_t limiter_upload_tables();
+cudaError_t adjoint_upload_tables();
 
 // launch shape of the stage kernel: cells per block (64, 128, 256) and the
 // number of blocks (0: one block per tile of cells; > 0: a persistent grid)
@@ -45,6 +46,21 @@ void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const d
 void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st);
 template <typename R>
 void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st);
+
+// adjoint of the operator: grad = (d L_h / d u)^T lam at the stage time t + tfac dt
+template <typename R>
+void launch_rhs_adjoint(int eq, int k, const MeshDev<R> &M, const R *u, const R *lam, R *grad, double tfac, const Ctl *ctl,
+                        cudaStream_t st);
+
+// adjoint of a limiter pass with frozen flags (flist, *nflag_dev): gout = gin
+// with the flagged cells' modes 1..np-1 replaced by the reconstruction's
+// transposed derivative contributions; u is the unlimited state of the pass
+template <typename R>
+void launch_limit_adjoint(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const int32_t *nflag_dev,
+                          const Ctl *ctl, double tfac, int w32, const R *gin, R *gout, int grid, cudaStream_t st);
+
+// out = a x + b y (y nullable) over n entries
+template <typename R> void launch_axpby(size_t n, R a, const R *x, R b, const R *y, R *out, int grid, cudaStream_t st);
 
 // read-only view of a solver for entry points outside api.cu (false: no mesh)
 bool solver_view(const struct ::cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area,
@@ -68,6 +84,6 @@ template <typename R>
 void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl,
                   double tfac, R *lim_out, int grid, int w32, cudaStream_t st);
 template <typename R>
-void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st);
+void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, Ctl *ctl, int grid, cudaStream_t st);
 
 }  // namespace csw

@@ -1304,9 +1304,10 @@ template void launch_limit<double>(int, int, const MeshDev<double> &, const doub
 // thread per (cell, coefficient), so the reads of lim_out are coalesced
 template <typename R>
 __global__ void k_scatter(int nv, int np, const int32_t *__restrict__ flist, const R *__restrict__ lim_out, R *__restrict__ u,
-                          const Ctl *__restrict__ ctl)
+                          Ctl *__restrict__ ctl)
 {
     if (!ctl->active) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nflag_sum += ctl->nflag;
     const int per = nv * (np - 1);
     const long long total = (long long)ctl->nflag * per;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
@@ -1316,12 +1317,556 @@ __global__ void k_scatter(int nv, int np, const int32_t *__restrict__ flist, con
 }
 
 template <typename R>
-void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, const Ctl *ctl, int grid, cudaStream_t st)
+void launch_scatter(int nv, int np, int ld, const int32_t *flist, const R *lim_out, R *u, Ctl *ctl, int grid, cudaStream_t st)
 {
     (void)ld;
     k_scatter<R><<<grid, 256, 0, st>>>(nv, np, flist, lim_out, u, ctl);
 }
-template void launch_scatter<float>(int, int, int, const int32_t *, const float *, float *, const Ctl *, int, cudaStream_t);
-template void launch_scatter<double>(int, int, int, const int32_t *, const double *, double *, const Ctl *, int, cudaStream_t);
+template void launch_scatter<float>(int, int, int, const int32_t *, const float *, float *, Ctl *, int, cudaStream_t);
+template void launch_scatter<double>(int, int, int, const int32_t *, const double *, double *, Ctl *, int, cudaStream_t);
+
+
+// ===========================================================================
+// Reverse mode of the reconstruction with the troubled-cell flags frozen
+// (the adjoint of a limiter pass).  All derivatives in W.
+// ===========================================================================
+
+// forward-mode number for the derivatives of the eigenvector entries
+template <typename T> struct Dual {
+    T v, d;
+    __host__ __device__ Dual(T a = T(0), T b = T(0)) : v(a), d(b) {}
+};
+template <typename T> __host__ __device__ inline Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <typename T> __host__ __device__ inline Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <typename T> __host__ __device__ inline Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <typename T> __host__ __device__ inline Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <typename T> __host__ __device__ inline Dual<T> operator/(Dual<T> a, Dual<T> b)
+{
+    const T q = a.v / b.v;
+    return {q, (a.d - q * b.d) / b.v};
+}
+template <typename T> __host__ __device__ inline Dual<T> rsqrt_(Dual<T> a)
+{
+    const T s = sqrt(a.v);
+    return {s, a.d / (T(2) * s)};
+}
+
+// dJ/d(ub) through the eigenvector row Ll and column Rr of one characteristic
+// field: sum_v Llb[v] dLl[v]/dub_k + Rrb[v] dRr[v]/dub_k, by one forward-mode
+// pass per component of ub
+template <typename W>
+__device__ __forceinline__ void eig_field_grad(const W *ub, W gam, W nx, W ny, int fl, const W (&Llb)[4], const W (&Rrb)[4], W (&out)[4])
+{
+    for (int k = 0; k < 4; ++k) {
+        Dual<W> U[4], L[4], Rv[4];
+        for (int v = 0; v < 4; ++v) U[v] = Dual<W>(ub[v], v == k ? W(1) : W(0));
+        euler_eig_field<Dual<W>>(U, Dual<W>(gam), Dual<W>(nx), Dual<W>(ny), fl, L, Rv);
+        W s = W(0);
+        for (int v = 0; v < 4; ++v) s += Llb[v] * L[v].d + Rrb[v] * Rv[v].d;
+        out[k] = s;
+    }
+}
+
+// reverse of weno_field: from mdb = dJ/dmd (modes 1..NP-1) to tb[f][i] +=
+// dJ/dt[f][i] and w0b += dJ/dw0; the forward quantities are recomputed here in W
+template <int K, typename R, typename W>
+__device__ __forceinline__ void weno_field_vjp(const R *__restrict__ op, const R (&t)[3][Ops<K>::NSUBK], R w0r,
+                                               const W (&mdb)[Deg<K>::NP - 1], W (&tb)[3][Ops<K>::NSUBK], W &w0b)
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NM = Deg<K>::NM, NSUBK = O::NSUBK, NL = (K == 1) ? 3 : 4;
+    const W eps = W(1e-10);
+    const W w0 = (W)w0r;
+    // ---- forward: Step 1 least-squares fits ----
+    W b2[3], b3[9], b4[15];
+    for (int s = 0; s < 3; ++s) b2[s] = (W)t[s][0] - w0;
+    b3[0] = b2[0]; b3[1] = b2[1]; b3[2] = b2[2];
+    for (int s = 0; s < 3; ++s) { b3[3 + 2 * s] = (W)t[s][1] - w0; b3[4 + 2 * s] = (W)t[s][2] - w0; }
+    if (K == 2) {
+        b4[0] = b2[0]; b4[1] = b2[1]; b4[2] = b2[2];
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i < 4; ++i) b4[3 + 4 * s + i] = (W)t[s][(3 + i) % NSUBK] - w0;
+    }
+    W q2[2], q3[5], q4[9];
+    for (int j = 0; j < 2; ++j) { W a = W(0); for (int s = 0; s < 3; ++s) a += (W)op[O::A2 + j * 3 + s] * b2[s]; q2[j] = a; }
+    for (int j = 0; j < 5; ++j) { W a = W(0); for (int s = 0; s < 9; ++s) a += (W)op[O::A3 + j * 9 + s] * b3[s]; q3[j] = a; }
+    if (K == 2)
+        for (int j = 0; j < 9; ++j) { W a = W(0); for (int s = 0; s < 15; ++s) a += (W)op[O::A4 + j * 15 + s] * b4[s]; q4[j] = a; }
+    // ---- Step 2 hierarchy ----
+    const R *gm = op + O::GAM;
+    const W g7 = (W)gm[7], g8 = (W)gm[8], g9 = (W)gm[9], g10 = (W)gm[10], g4 = (W)gm[4], g5 = (W)gm[5];
+    W p[3][NM];
+    for (int l = 0; l < 3; ++l) for (int j = 0; j < NM; ++j) p[l][j] = W(0);
+    for (int j = 0; j < 2; ++j) p[0][j] = q2[j] * g7;
+    for (int j = 0; j < 5; ++j) p[1][j] = (q3[j] - g10 * p[0][j]) * g8;
+    if (K == 2) for (int j = 0; j < 9; ++j) p[2][j] = (q4[j] - g4 * p[0][j] - g5 * p[1][j]) * g9;
+    // ---- Step 3 smoothness indicators: y = L^T p_l, beta = |y|^2 ----
+    const R *L = op + O::LH;
+    const int nn[3] = {2, 5, 9};
+    W y[3][NM], beta[4];
+    for (int l = 0; l < NL - 1; ++l) {
+        W acc = W(0);
+        for (int j = 0; j < nn[l]; ++j) {
+            W a = W(0);
+            for (int i = j; i < nn[l]; ++i) a += (W)L[i * (i + 1) / 2 + j] * p[l][i];
+            y[l][j] = a;
+            acc += a * a;
+        }
+        beta[l + 1] = acc;
+    }
+    // beta_1 magnified (sigma weights in quotient form: the same normalised weights)
+    W al[3], bl[3], b1[3], e[3];
+    for (int f = 0; f < 3; ++f) {
+        const W r1 = (W)t[f][1] - (W)t[f][0], r2 = (W)t[f][2] - (W)t[f][0];
+        al[f] = (W)op[O::MI + 4 * f + 0] * r1 + (W)op[O::MI + 4 * f + 1] * r2;
+        bl[f] = (W)op[O::MI + 4 * f + 2] * r1 + (W)op[O::MI + 4 * f + 3] * r2;
+        b1[f] = al[f] * al[f] + bl[f] * bl[f];
+        e[f] = b1[f] + eps;
+    }
+    const W d01 = b1[0] - b1[1], d12 = b1[1] - b1[2], d20 = b1[2] - b1[0];
+    const W D = (d01 * d01 + d12 * d12 + d20 * d20) / W(3), D2 = D * D;
+    W sg[3], Ss = W(0);
+    for (int f = 0; f < 3; ++f) { sg[f] = W(1) + D2 / e[f]; Ss += sg[f]; }
+    W ab = W(0), bb = W(0);
+    for (int f = 0; f < 3; ++f) { ab += sg[f] * al[f]; bb += sg[f] * bl[f]; }
+    ab /= Ss;
+    bb /= Ss;
+    beta[0] = ab * ab + bb * bb;
+    // ---- Step 4 tau and weights (quotient form) ----
+    const W ctau = (K == 1) ? W(0.25) : W(1.0 / 16.0);
+    W tau = W(0);
+    for (int l = 0; l < NL - 1; ++l) { const W d = beta[NL - 1] - beta[l]; tau += d * d; }
+    tau *= ctau;
+    const R *gl = gm + ((K == 1) ? 0 : 3);
+    W a[4], z[4], om[4], Sz = W(0);
+    for (int l = 0; l < NL; ++l) { a[l] = eps + beta[l]; z[l] = (W)gl[l] * (W(1) + tau / a[l]); Sz += z[l]; }
+    for (int l = 0; l < NL; ++l) om[l] = z[l] / Sz;
+    // ---- reverse: Step 5 projection ----
+    W cmb[NM];
+    for (int j = 0; j < NM; ++j) {
+        W s = W(0);
+        for (int i = 0; i < NP - 1; ++i) s += (W)op[O::PHI + i * NM + j] * mdb[i];
+        cmb[j] = s;
+    }
+    W omb[4] = {W(0), W(0), W(0), W(0)}, pb[3][NM];
+    for (int l = 0; l < 3; ++l)
+        for (int j = 0; j < NM; ++j) pb[l][j] = W(0);
+    for (int l = 1; l < NL; ++l) {
+        W s = W(0);
+        for (int j = 0; j < NM; ++j) { s += cmb[j] * p[l - 1][j]; pb[l - 1][j] = om[l] * cmb[j]; }
+        omb[l] = s;
+    }
+    // ---- Step 4 reverse ----
+    W dot = W(0);
+    for (int l = 0; l < NL; ++l) dot += omb[l] * om[l];
+    W betab[4] = {W(0), W(0), W(0), W(0)}, taub = W(0);
+    for (int l = 0; l < NL; ++l) {
+        const W zb = (omb[l] - dot) / Sz;
+        taub += zb * (W)gl[l] / a[l];
+        betab[l] += -zb * (W)gl[l] * tau / (a[l] * a[l]);
+    }
+    for (int l = 0; l < NL - 1; ++l) {
+        const W d = beta[NL - 1] - beta[l];
+        betab[l] -= W(2) * ctau * d * taub;
+        betab[NL - 1] += W(2) * ctau * d * taub;
+    }
+    // ---- Step 3 reverse: beta_l = |L^T p|^2 -> p_b += 2 beta_b L y ----
+    for (int l = 0; l < NL - 1; ++l)
+        for (int i = 0; i < nn[l]; ++i) {
+            W s = W(0);
+            for (int j = 0; j <= i; ++j) s += (W)L[i * (i + 1) / 2 + j] * y[l][j];
+            pb[l][i] += W(2) * betab[l + 1] * s;
+        }
+    // beta_1 magnification reverse
+    {
+        const W abb = W(2) * ab * betab[0], bbb = W(2) * bb * betab[0];
+        W alb[3], blb[3], b1b[3], sgb[3];
+        for (int f = 0; f < 3; ++f) {
+            alb[f] = abb * sg[f] / Ss;
+            blb[f] = bbb * sg[f] / Ss;
+            sgb[f] = (abb * (al[f] - ab) + bbb * (bl[f] - bb)) / Ss;
+        }
+        W D2b = W(0);
+        for (int f = 0; f < 3; ++f) { b1b[f] = -sgb[f] * D2 / (e[f] * e[f]); D2b += sgb[f] / e[f]; }
+        const W Db = W(2) * D * D2b;
+        b1b[0] += Db * (W(2) * d01 - W(2) * d20) / W(3);
+        b1b[1] += Db * (W(2) * d12 - W(2) * d01) / W(3);
+        b1b[2] += Db * (W(2) * d20 - W(2) * d12) / W(3);
+        for (int f = 0; f < 3; ++f) {
+            alb[f] += W(2) * al[f] * b1b[f];
+            blb[f] += W(2) * bl[f] * b1b[f];
+            const W r1b = (W)op[O::MI + 4 * f + 0] * alb[f] + (W)op[O::MI + 4 * f + 2] * blb[f];
+            const W r2b = (W)op[O::MI + 4 * f + 1] * alb[f] + (W)op[O::MI + 4 * f + 3] * blb[f];
+            tb[f][1] += r1b;
+            tb[f][2] += r2b;
+            tb[f][0] -= r1b + r2b;
+        }
+    }
+    // ---- Step 2 reverse ----
+    W q2b[2], q3b[5], q4b[9];
+    if (K == 2)
+        for (int j = 0; j < 9; ++j) {
+            q4b[j] = g9 * pb[2][j];
+            pb[0][j] -= g4 * g9 * pb[2][j];
+            pb[1][j] -= g5 * g9 * pb[2][j];
+        }
+    for (int j = 0; j < 5; ++j) {
+        q3b[j] = g8 * pb[1][j];
+        pb[0][j] -= g10 * g8 * pb[1][j];
+    }
+    for (int j = 0; j < 2; ++j) q2b[j] = g7 * pb[0][j];
+    // ---- Step 1 reverse ----
+    W sumb = W(0);
+    for (int s = 0; s < 3; ++s) {
+        W bs = W(0);
+        for (int j = 0; j < 2; ++j) bs += (W)op[O::A2 + j * 3 + s] * q2b[j];
+        tb[s][0] += bs;
+        sumb += bs;
+    }
+    for (int s = 0; s < 9; ++s) {
+        W bs = W(0);
+        for (int j = 0; j < 5; ++j) bs += (W)op[O::A3 + j * 9 + s] * q3b[j];
+        if (s < 3) tb[s][0] += bs;
+        else tb[(s - 3) / 2][1 + ((s - 3) & 1)] += bs;
+        sumb += bs;
+    }
+    if (K == 2)
+        for (int s = 0; s < 15; ++s) {
+            W bs = W(0);
+            for (int j = 0; j < 9; ++j) bs += (W)op[O::A4 + j * 15 + s] * q4b[j];
+            if (s < 3) tb[s][0] += bs;
+            else tb[(s - 3) / 4][(3 + (s - 3) % 4) % NSUBK] += bs;
+            sumb += bs;
+        }
+    w0b -= sumb;
+}
+
+// One lane (direction d, characteristic field fl) of the reverse of
+// limit_cell_euler_lane: rb = dJ/d(reconstructed modes 1..NP-1) of the cell.
+// Adds to own[v][m] (the cell's own modes: the mean through the eigenvectors
+// and w0, all modes through mirrored ghosts) and nb[f][v][m] (face f's
+// neighbour).
+template <int K, typename R, typename W>
+__device__ __forceinline__ void limit_lane_euler_vjp(const MeshDev<R> &M, const R *__restrict__ u, const R *__restrict__ op, int c,
+                                                     double tl, int lane8, const W (&rb)[4][Deg<K>::NP - 1], W (&own)[4][Deg<K>::NP],
+                                                     W (&nb)[3][4][Deg<K>::NP])
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NSUBK = O::NSUBK;
+    const int ld = M.ldc;
+    const int d = lane8 >> 2, fl = lane8 & 3;
+    const R is2 = R(0.70710678118654752440);
+    R u0[4][NP];
+    load_cell<4, NP>(u, c, u0);
+    R ub[4];
+    for (int v = 0; v < 4; ++v) ub[v] = u0[v][0] * is2;
+    R Ll[4], Rr[4];
+    const R nxd = d == 0 ? R(1) : R(0), nyd = d == 0 ? R(0) : R(1);
+    euler_eig_field<R>(ub, M.gammar, nxd, nyd, fl, Ll, Rr);
+    // forward: characteristic subcell means
+    R tc[3][NSUBK], wcs[3][NP], S[3][4];
+    int kinds[3], codes[3];
+    for (int f = 0; f < 3; ++f) {
+        const int code = M.nbr[f * ld + c];
+        codes[f] = code;
+        kinds[f] = -1;  // internal
+        if (code >= 0) {
+            R wn[4][NP];
+            load_cell<4, NP>(u, code, wn);
+            for (int m = 0; m < NP; ++m) {
+                R s = R(0);
+                for (int v = 0; v < 4; ++v) s += Ll[v] * wn[v][m];
+                wcs[f][m] = s;
+            }
+        } else {
+            const BFace bf = M.bf[-code - 1];
+            kinds[f] = M.bc->kind[bf.tag];
+            if (kinds[f] == BC_DIRICHLET || kinds[f] == BC_SHOCKLINE) {
+                R dummy[4] = {R(0), R(0), R(0), R(0)};
+                ghost<EULER, R>(bf, M.bc, 0.5, tl, dummy, S[f]);
+                R sc = R(0);
+                for (int v = 0; v < 4; ++v) sc += Ll[v] * S[f][v];
+                for (int i = 0; i < NSUBK; ++i) tc[f][i] = sc;
+                continue;
+            }
+            const R nx = (R)bf.nx, ny = (R)bf.ny;
+            for (int m = 0; m < NP; ++m) {
+                R w1 = u0[1][m], w2 = u0[2][m];
+                if (kinds[f] == BC_WALL) {
+                    const R mn = w1 * nx + w2 * ny;
+                    w1 -= R(2) * mn * nx;
+                    w2 -= R(2) * mn * ny;
+                }
+                wcs[f][m] = Ll[0] * u0[0][m] + Ll[1] * w1 + Ll[2] * w2 + Ll[3] * u0[3][m];
+            }
+        }
+        for (int i = 0; i < NSUBK; ++i) {
+            R s = R(0);
+            for (int m = 0; m < NP; ++m) s += op[O::W + (f * NSUBK + i) * NP + m] * wcs[f][m];
+            tc[f][i] = s;
+        }
+    }
+    R w0 = R(0);
+    for (int v = 0; v < 4; ++v) w0 += Ll[v] * ub[v];
+    R md[NP - 1];
+    weno_field<K, R, W>(op, tc, w0, md);
+    // reverse: res[v][i] = 1/2 Rr[v] md[i]
+    W mdb[NP - 1], Rrb[4], Llb[4], ubb[4];
+    for (int i = 0; i < NP - 1; ++i) {
+        W s = W(0);
+        for (int v = 0; v < 4; ++v) s += W(0.5) * (W)Rr[v] * rb[v][i];
+        mdb[i] = s;
+    }
+    for (int v = 0; v < 4; ++v) {
+        W s = W(0);
+        for (int i = 0; i < NP - 1; ++i) s += W(0.5) * (W)md[i] * rb[v][i];
+        Rrb[v] = s;
+    }
+    W tcb[3][NSUBK], w0b = W(0);
+    for (int f = 0; f < 3; ++f)
+        for (int i = 0; i < NSUBK; ++i) tcb[f][i] = W(0);
+    weno_field_vjp<K, R, W>(op, tc, w0, mdb, tcb, w0b);
+    for (int v = 0; v < 4; ++v) { Llb[v] = w0b * (W)ub[v]; ubb[v] = w0b * (W)Ll[v]; }
+    for (int f = 0; f < 3; ++f) {
+        if (kinds[f] == BC_DIRICHLET || kinds[f] == BC_SHOCKLINE) {
+            W s = W(0);
+            for (int i = 0; i < NSUBK; ++i) s += tcb[f][i];
+            for (int v = 0; v < 4; ++v) Llb[v] += s * (W)S[f][v];
+            continue;
+        }
+        W wcb[NP];
+        for (int m = 0; m < NP; ++m) {
+            W s = W(0);
+            for (int i = 0; i < NSUBK; ++i) s += (W)op[O::W + (f * NSUBK + i) * NP + m] * tcb[f][i];
+            wcb[m] = s;
+        }
+        if (codes[f] >= 0) {
+            R wn[4][NP];
+            load_cell<4, NP>(u, codes[f], wn);
+            for (int v = 0; v < 4; ++v)
+                for (int m = 0; m < NP; ++m) {
+                    nb[f][v][m] += (W)Ll[v] * wcb[m];
+                    Llb[v] += wcb[m] * (W)wn[v][m];
+                }
+        } else {
+            const BFace bf = M.bf[-codes[f] - 1];
+            const W nx = (W)(R)bf.nx, ny = (W)(R)bf.ny;
+            for (int m = 0; m < NP; ++m) {
+                W w1 = (W)u0[1][m], w2 = (W)u0[2][m];
+                W g1 = (W)Ll[1] * wcb[m], g2 = (W)Ll[2] * wcb[m];
+                if (kinds[f] == BC_WALL) {
+                    const W mn = w1 * nx + w2 * ny, gn = g1 * nx + g2 * ny;
+                    w1 -= W(2) * mn * nx;
+                    w2 -= W(2) * mn * ny;
+                    g1 -= W(2) * gn * nx;  // the reflection is symmetric
+                    g2 -= W(2) * gn * ny;
+                }
+                own[0][m] += (W)Ll[0] * wcb[m];
+                own[1][m] += g1;
+                own[2][m] += g2;
+                own[3][m] += (W)Ll[3] * wcb[m];
+                Llb[0] += wcb[m] * (W)u0[0][m];
+                Llb[1] += wcb[m] * w1;
+                Llb[2] += wcb[m] * w2;
+                Llb[3] += wcb[m] * (W)u0[3][m];
+            }
+        }
+    }
+    W ubw[4], eg[4];
+    for (int v = 0; v < 4; ++v) ubw[v] = (W)ub[v];
+    eig_field_grad<W>(ubw, (W)M.gammar, (W)nxd, (W)nyd, fl, Llb, Rrb, eg);
+    for (int v = 0; v < 4; ++v) own[v][0] += (ubb[v] + eg[v]) * (W)is2;
+}
+
+// Burgers: one lane per flagged cell, the reverse of limit_cell
+template <int K, typename R, typename W>
+__device__ __forceinline__ void limit_cell_burgers_vjp(const MeshDev<R> &M, const R *__restrict__ u, const R *__restrict__ op, int c,
+                                                       double tl, const W (&rb)[Deg<K>::NP - 1], W (&own)[Deg<K>::NP],
+                                                       W (&nb)[3][Deg<K>::NP])
+{
+    using O = Ops<K>;
+    constexpr int NP = Deg<K>::NP, NSUBK = O::NSUBK;
+    const int ld = M.ldc;
+    R u0[NP];
+    for (int m = 0; m < NP; ++m) u0[m] = u[sidx(1, NP, 0, m, c)];
+    R t[3][NSUBK];
+    int codes[3], kinds[3];
+    for (int f = 0; f < 3; ++f) {
+        const int code = M.nbr[f * ld + c];
+        codes[f] = code;
+        kinds[f] = -1;
+        R w[NP];
+        if (code >= 0) {
+            for (int m = 0; m < NP; ++m) w[m] = u[sidx(1, NP, 0, m, code)];
+        } else {
+            const BFace bf = M.bf[-code - 1];
+            kinds[f] = M.bc->kind[bf.tag];
+            if (kinds[f] == BC_DIRICHLET || kinds[f] == BC_SHOCKLINE) {
+                R Sv[1], dummy[1] = {R(0)};
+                ghost<BURGERS, R>(bf, M.bc, 0.5, tl, dummy, Sv);
+                for (int i = 0; i < NSUBK; ++i) t[f][i] = Sv[0];
+                continue;
+            }
+            for (int m = 0; m < NP; ++m) w[m] = u0[m];
+        }
+        for (int i = 0; i < NSUBK; ++i) {
+            R s = R(0);
+            for (int m = 0; m < NP; ++m) s += op[O::W + (f * NSUBK + i) * NP + m] * w[m];
+            t[f][i] = s;
+        }
+    }
+    const R w0 = u0[0] * R(0.70710678118654752440);
+    W tb[3][NSUBK], w0b = W(0);
+    for (int f = 0; f < 3; ++f)
+        for (int i = 0; i < NSUBK; ++i) tb[f][i] = W(0);
+    weno_field_vjp<K, R, W>(op, t, w0, rb, tb, w0b);
+    own[0] += w0b * W(0.70710678118654752440);
+    for (int f = 0; f < 3; ++f) {
+        if (kinds[f] == BC_DIRICHLET || kinds[f] == BC_SHOCKLINE) continue;
+        for (int m = 0; m < NP; ++m) {
+            W s = W(0);
+            for (int i = 0; i < NSUBK; ++i) s += (W)op[O::W + (f * NSUBK + i) * NP + m] * tb[f][i];
+            if (codes[f] >= 0) nb[f][m] += s;
+            else own[m] += s;
+        }
+    }
+}
+
+// Adjoint of one limiter pass with the flags of the forward pass frozen:
+// gout (prepared by the caller as gin with the flagged cells' modes 1..NP-1
+// zeroed) += the reconstruction's transposed derivative applied to gin's
+// modes 1..NP-1 of every flagged cell.  u: the state the forward pass
+// reconstructed from (before it was limited).  A reconstruction that the
+// forward pass replaced by the cell mean (positivity fallback) contributes
+// nothing.  Contributions to shared neighbours are added atomically.
+template <int EQ, int K, typename R, typename W>
+__global__ void __launch_bounds__(128) k_limit_adj(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ ops,
+                                                   const int32_t *__restrict__ flist, const int32_t *__restrict__ nflag_dev,
+                                                   const Ctl *__restrict__ ctl, double tfac, const R *__restrict__ gin, R *gout)
+{
+    constexpr int NP = Deg<K>::NP, NV = Eqn<EQ>::NV;
+    constexpr int G = (EQ == EULER) ? 8 : 1;
+    const int n = *nflag_dev;
+    const double tl = stage_time(ctl, tfac);
+    const int warp0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = warp0; base / G < n; base += stride) {  // trip count uniform across the warp
+        const int idx = (base + lane) / G;
+        const bool active = idx < n;
+        const int c = active ? flist[idx] : 0;
+        const R *op = ops + (size_t)c * Ops<K>::SIZE;
+        if (EQ == EULER) {
+            // forward result of the cell, to see whether the positivity fallback applied
+            R res[4][NP - 1];
+            for (int v = 0; v < 4; ++v)
+                for (int i = 0; i < NP - 1; ++i) res[v][i] = R(0);
+            if (active) limit_cell_euler_lane<K, R, W>(M, u, op, c, tl, lane & 7, res);
+            for (int v = 0; v < 4; ++v)
+                for (int i = 0; i < NP - 1; ++i) {
+                    R x = res[v][i];
+                    x += __shfl_xor_sync(0xffffffffu, x, 1);
+                    x += __shfl_xor_sync(0xffffffffu, x, 2);
+                    x += __shfl_xor_sync(0xffffffffu, x, 4);
+                    res[v][i] = x;
+                }
+            bool bad = false;
+            if (active) {
+                R m0[4];
+                for (int v = 0; v < 4; ++v) m0[v] = u[sidx(4, NP, v, 0, c)];
+                bad = positivity_bad_lane<K, R>(m0, res, lane & 7, M.gamma);
+            }
+            const unsigned grp = (__ballot_sync(0xffffffffu, bad) >> (lane & ~7)) & 0xffu;
+            W own[4][NP], nbg[3][4][NP], rb[4][NP - 1];
+            for (int v = 0; v < 4; ++v)
+                for (int m = 0; m < NP; ++m) {
+                    own[v][m] = W(0);
+                    for (int f = 0; f < 3; ++f) nbg[f][v][m] = W(0);
+                }
+            if (active && !grp) {
+                for (int v = 0; v < 4; ++v)
+                    for (int i = 0; i < NP - 1; ++i) rb[v][i] = (W)gin[sidx(4, NP, v, i + 1, c)];
+                limit_lane_euler_vjp<K, R, W>(M, u, op, c, tl, lane & 7, rb, own, nbg);
+            }
+            // sum the eight lanes' contributions; lane 0 of the group adds them
+            for (int v = 0; v < 4; ++v)
+                for (int m = 0; m < NP; ++m) {
+                    W x = own[v][m];
+                    x += __shfl_xor_sync(0xffffffffu, x, 1);
+                    x += __shfl_xor_sync(0xffffffffu, x, 2);
+                    x += __shfl_xor_sync(0xffffffffu, x, 4);
+                    own[v][m] = x;
+                    for (int f = 0; f < 3; ++f) {
+                        W y = nbg[f][v][m];
+                        y += __shfl_xor_sync(0xffffffffu, y, 1);
+                        y += __shfl_xor_sync(0xffffffffu, y, 2);
+                        y += __shfl_xor_sync(0xffffffffu, y, 4);
+                        nbg[f][v][m] = y;
+                    }
+                }
+            if (active && !grp && (lane & 7) == 0) {
+                for (int v = 0; v < 4; ++v)
+                    for (int m = 0; m < NP; ++m) atomicAdd(&gout[sidx(4, NP, v, m, c)], (R)own[v][m]);
+                for (int f = 0; f < 3; ++f) {
+                    const int code = M.nbr[f * M.ldc + c];
+                    if (code < 0) continue;
+                    for (int v = 0; v < 4; ++v)
+                        for (int m = 0; m < NP; ++m) atomicAdd(&gout[sidx(4, NP, v, m, code)], (R)nbg[f][v][m]);
+                }
+            }
+        } else if (active) {
+            W rb[NP - 1], own[NP], nbg[3][NP];
+            for (int i = 0; i < NP - 1; ++i) rb[i] = (W)gin[sidx(1, NP, 0, i + 1, c)];
+            for (int m = 0; m < NP; ++m) {
+                own[m] = W(0);
+                for (int f = 0; f < 3; ++f) nbg[f][m] = W(0);
+            }
+            limit_cell_burgers_vjp<K, R, W>(M, u, op, c, tl, rb, own, nbg);
+            for (int m = 0; m < NP; ++m) atomicAdd(&gout[sidx(1, NP, 0, m, c)], (R)own[m]);
+            for (int f = 0; f < 3; ++f) {
+                const int code = M.nbr[f * M.ldc + c];
+                if (code < 0) continue;
+                for (int m = 0; m < NP; ++m) atomicAdd(&gout[sidx(1, NP, 0, m, code)], (R)nbg[f][m]);
+            }
+        }
+    }
+}
+
+// zero modes 1..np-1 of the listed cells (the limited modes do not pass through)
+template <typename R>
+__global__ void k_zero_flagged(int nv, int np, const int32_t *__restrict__ flist, const int32_t *__restrict__ nflag_dev, R *g)
+{
+    const int n = *nflag_dev;
+    const int per = nv * (np - 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * per; t += (long long)gridDim.x * blockDim.x) {
+        const int idx = (int)(t / per), r = (int)(t % per);
+        g[sidx(nv, np, r / (np - 1), r % (np - 1) + 1, flist[idx])] = R(0);
+    }
+}
+
+template <typename R>
+void launch_limit_adjoint(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const int32_t *nflag_dev,
+                          const Ctl *ctl, double tfac, int w32, const R *gin, R *gout, int grid, cudaStream_t st)
+{
+    const int nv = (eq == EULER) ? 4 : 1, np = (k == 1) ? 3 : 6;
+    k_zero_flagged<R><<<grid, 256, 0, st>>>(nv, np, flist, nflag_dev, gout);
+#define CSW_LA(E, KK, WW) k_limit_adj<E, KK, R, WW><<<grid, 128, 0, st>>>(M, u, ops, flist, nflag_dev, ctl, tfac, gin, gout)
+    if (sizeof(R) == 4 && w32) {
+        if (eq == BURGERS && k == 1) CSW_LA(BURGERS, 1, float);
+        else if (eq == BURGERS) CSW_LA(BURGERS, 2, float);
+        else if (k == 1) CSW_LA(EULER, 1, float);
+        else CSW_LA(EULER, 2, float);
+    } else {
+        if (eq == BURGERS && k == 1) CSW_LA(BURGERS, 1, double);
+        else if (eq == BURGERS) CSW_LA(BURGERS, 2, double);
+        else if (k == 1) CSW_LA(EULER, 1, double);
+        else CSW_LA(EULER, 2, double);
+    }
+#undef CSW_LA
+}
+template void launch_limit_adjoint<float>(int, int, const MeshDev<float> &, const float *, const float *, const int32_t *,
+                                          const int32_t *, const Ctl *, double, int, const float *, float *, int, cudaStream_t);
+template void launch_limit_adjoint<double>(int, int, const MeshDev<double> &, const double *, const double *, const int32_t *,
+                                           const int32_t *, const Ctl *, double, int, const double *, double *, int, cudaStream_t);
 
 }  // namespace csw

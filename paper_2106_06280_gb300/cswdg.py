@@ -66,6 +66,9 @@ def _load():
         "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
         "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
         "cswdg_autotune": ([vp, dp, C.POINTER(i32)], C.c_int),
+        "cswdg_rhs_adjoint": ([vp, C.c_double, dp, dp, dp], C.c_int),
+        "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp], C.c_int),
+        "cswdg_limit_adjoint": ([vp, C.c_double, dp, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
         "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -81,7 +84,8 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_launches_per_step", "cswdg_get_time",
             "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
-            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_autotune",
+            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_autotune", "cswdg_rhs_adjoint",
+            "cswdg_adjoint_steps", "cswdg_limit_adjoint",
             "cswdg_set_stage_shape"]
 TUNE_CANDIDATES = 7
 
@@ -222,6 +226,29 @@ class Solver:
         out = np.zeros_like(modes)
         self._chk(lib.cswdg_eval_rhs(self.h, t, _p(modes), _p(out)))
         return out
+
+    def rhs_adjoint(self, modes, lam, t=0.0):
+        """(dL_h/du)^T lam at the state modes (user basis and cell order)."""
+        modes, lam = _d(modes), _d(lam)
+        out = np.zeros_like(modes)
+        self._chk(lib.cswdg_rhs_adjoint(self.h, t, _p(modes), _p(lam), _p(out)))
+        return out
+
+    def adjoint_steps(self, u0, gT, dt, nsteps, checkpoint_every=20):
+        """Run nsteps fixed-dt steps from u0 and return (u_N, (du_N/du_0)^T gT)."""
+        u0, gT = _d(u0), _d(gT)
+        uT = np.zeros_like(u0)
+        g0 = np.zeros_like(u0)
+        self._chk(lib.cswdg_adjoint_steps(self.h, dt, nsteps, checkpoint_every, _p(u0), _p(gT), _p(uT), _p(g0)))
+        return uT, g0
+
+    def limit_adjoint(self, modes, lam, t=0.0):
+        """(dLim/du)^T lam at the state modes with the flags frozen; returns (grad, flags)."""
+        modes, lam = _d(modes), _d(lam)
+        out = np.zeros_like(modes)
+        fl = np.zeros(self.nc, dtype=np.uint8)
+        self._chk(lib.cswdg_limit_adjoint(self.h, t, _p(modes), _p(lam), _p(out), _p(fl, C.c_uint8)))
+        return out, fl
 
     def limit(self, modes, t=0.0):
         modes = _d(modes)
