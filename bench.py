@@ -59,6 +59,26 @@ def dist_info():
     return ws, rk, lr
 
 
+def replica_seed(rank: int) -> int:
+    """Mesh/initial-condition seed of a rank's replica (replicas only: each GPU
+    advances its own independent copy of the workload)."""
+    return 3 + rank
+
+
+def max_over_ranks(ms: float, device: str) -> float:
+    """The slowest rank's timed-region milliseconds (the only collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, ms_max: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return units_per_rank * world_size / (ms_max * 1e-3)
+
+
 def stage_bytes_per_cell(fp32: bool) -> float:
     """Algorithmic DRAM bytes of the operator + RK stage kernel per cell,
     averaged over the three stages: read u^(i-1) (S), write u^(i) (S), read u^n
@@ -183,7 +203,7 @@ def run_ours(args):
     from paper_2106_06280_gb300 import cswdg as csw
 
     stream = torch.cuda.current_stream().cuda_stream
-    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=3 + rk, workload=args.workload, shape=args.stage_shape)
+    pb, s = setup_solver(csw, csw.FP32_BULK, stream, seed=replica_seed(rk), workload=args.workload, shape=args.stage_shape)
     shape = s.shape
     nc = pb.mesh.nc
     t_end = pb.t_end
@@ -209,12 +229,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop(lr) if rk == 0 else None
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    units = float(nc) * NP * NV * 3 * args.steps * ws
-    value = units / (ms * 1e-3)
+        ms = max_over_ranks(ms, "cuda")
+    value = whole_job_rate(float(nc) * NP * NV * 3 * args.steps, ws, ms)
     nflag = s.num_flagged()
 
     # per-kernel device time (events after every launch, no graph), same state trajectory
@@ -247,7 +263,7 @@ def run_ours(args):
         """The same workload in another precision mode, device-timed like value."""
         if nsteps <= 0:
             return None
-        _, s2 = setup_solver(csw, precision, stream, seed=3 + rk, workload=args.workload, shape=args.stage_shape)
+        _, s2 = setup_solver(csw, precision, stream, seed=replica_seed(rk), workload=args.workload, shape=args.stage_shape)
         s2.step(0.0, args.warmup, t_end)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
