@@ -517,3 +517,33 @@ def test_convergence_p2_all_cells_limited():
     own meshes; see the P2 top-polynomial reading)."""
     e = _burgers_errors(2, 2, [8, 16, 32])
     assert np.log2(e[-2] / e[-1]) > 2.0, e
+
+
+def test_oracle_central_differences_are_a_usable_adjoint_reference():
+    """The GPU adjoint tests compare with central differences of the oracle.
+    Pin that reference: on the states those tests use, the operator and a
+    KXRCF + CSWENO pass are smooth enough that eps = 1e-5 and 1e-6 give the same
+    directional derivative (operator: 1e-6 relative; limiter pass, flags
+    unchanged: 5e-6, below the 1e-5 the GPU limiter-adjoint tests use), and the
+    directional derivative of the operator is linear in the direction."""
+    pb = W.riemann_quadrants(9, seed=14)
+    nc = pb.mesh.nc
+    area = np.sqrt(W.cell_areas(pb.mesh))[:, None, None]
+    u = W.random_modes(pb.mesh, 4, 6, 302)
+    lam = (W.uniform01(811, np.arange(nc * 24)).reshape(nc, 4, 6) * 2 - 1) * area
+    d1 = (W.uniform01(821, np.arange(nc * 24)).reshape(nc, 4, 6) * 2 - 1) * 0.3 * area
+    d2 = (W.uniform01(831, np.arange(nc * 24)).reshape(nc, 4, 6) * 2 - 1) * 0.3 * area
+    o = oracle.Oracle(pb, k=2, limiter=1)
+
+    def fd(f, d, eps):
+        return (np.sum(lam * f(u + eps * d)) - np.sum(lam * f(u - eps * d))) / (2 * eps)
+
+    L = lambda v: o.rhs(v, 0.017)
+    a, b = fd(L, d1, 1e-5), fd(L, d1, 1e-6)
+    assert abs(a - b) < 1e-6 * abs(b)
+    assert abs(fd(L, d1 + d2, 1e-6) - (b + fd(L, d2, 1e-6))) < 1e-6 * abs(b)
+    f0 = o.limit(u, 0.0)[1]
+    Lim = lambda v: o.limit(v, 0.0)[0]
+    assert np.array_equal(o.limit(u + 1e-5 * d1, 0.0)[1], f0) and np.array_equal(o.limit(u - 1e-5 * d1, 0.0)[1], f0)
+    a, b = fd(Lim, d1, 1e-5), fd(Lim, d1, 1e-6)
+    assert abs(a - b) < 5e-6 * abs(b)
