@@ -84,12 +84,13 @@ def stage_bytes_per_cell(fp32: bool) -> float:
     averaged over the three stages: read u^(i-1) (S), write u^(i) (S), read u^n
     (S, stages 2 and 3), geometry (4 inverse-Jacobian + 9 scaled-normal words),
     three neighbour indices (12 B), the packed neighbour faces (1 B) and the
-    8 KXRCF precursor words written for the detection.  Neighbour traces are
-    reuse of data already counted."""
+    KXRCF precursors written for the detection (8 words in the cell's record,
+    3 face means into the neighbours' records).  Neighbour traces are reuse of
+    data already counted."""
     s = 4 if fp32 else 8
     S = NP * NV * s
     geo = 13 * s + 12 + 1
-    kx = 8 * s
+    kx = 11 * s
     return (3 * (2 * S + geo + kx) + 2 * S) / 3.0
 
 
@@ -306,6 +307,27 @@ def run_ours(args):
                 "note": "forward with checkpoints + recomputation + reverse sweep, host buffers in and out; "
                         "value counts the forward DOF-stage updates once"}
 
+    def l1_vs_fp64(nsteps):
+        """FP32-bulk against FP64 on the same GPU: both from the same projected,
+        every-cell-limited initial state, nsteps steps of the same fixed dt (half
+        the FP64 CFL step), then the area-weighted L1 difference of the density
+        means relative to the L1 norm of the FP64 density means."""
+        if nsteps <= 0:
+            return None
+        res = {}
+        for name, prec in (("fp64", csw.FP64), ("fp32_bulk", csw.FP32_BULK)):
+            pbl, sl = setup_solver(csw, prec, stream, seed=replica_seed(rk), workload=args.workload, shape=args.stage_shape)
+            if name == "fp64":
+                dtl = 0.5 * sl.cfl_dt()
+            sl.set_time(0.0)
+            sl.step(dtl, nsteps, 1e300)
+            res[name] = sl.read_modes()[:, 0, 0]
+            sl.close()
+        area = W.cell_areas(pbl.mesh)
+        rho64, rho32 = res["fp64"] / np.sqrt(area), res["fp32_bulk"] / np.sqrt(area)
+        return {"steps": nsteps, "dt": dtl, "quantity": "density cell means",
+                "l1_rel": float(np.sum(area * np.abs(rho32 - rho64)) / np.sum(area * np.abs(rho64)))}
+
     adj = adjoint(args.adjoint_steps)
     fp32 = secondary(csw.FP32, args.fp32_steps, "FP32 mode: smoothness indicators and nonlinear weights in float as well "
                                                  "(quotient forms), FP64 only for close calls of the decisions")
@@ -339,6 +361,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "adjoint": adj,
+        "fp32_bulk_vs_fp64_l1": l1_vs_fp64(args.l1_steps),
         "fp32_weights": fp32,
         "fp64": fp64,
     }
@@ -418,6 +441,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--fp32-steps", type=int, default=10)
     ap.add_argument("--adjoint-steps", type=int, default=100)
+    ap.add_argument("--l1-steps", type=int, default=20)
     ap.add_argument("--stage-shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
                     help="cells per block and grid of the stage kernel (e.g. 256,304); default: autotune")
     ap.add_argument("--cpu-sample", type=int, default=200000)

@@ -444,7 +444,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     A_(dalloc(&s->flags_user, (size_t)ld));
     A_(dalloc(&s->flist, (size_t)ld));
     A_(cudaMalloc(&s->lim_out, (size_t)nc * s->nv * (s->np - 1) * rs));
-    A_(cudaMalloc(&s->kx, (size_t)ld * KX_COUNT * rs));
+    A_(cudaMalloc(&s->kx, (size_t)ld * KX_STRIDE * rs));
     A_(dalloc(&s->ctl, 1));
     A_(dalloc(&s->dev_user, std::max((size_t)nc * s->nv * s->np, (size_t)nc * 7 * s->nv)));
     A_(dalloc(&s->cons_part, (size_t)s->nv * ((nc + 255) / 256)));

@@ -967,19 +967,12 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
     if (c < M.nc) {
         const int ld = M.ldc;
         // every load of the thread is issued before the first use: the neighbour
-        // ids and their face means (one dependent level), the own precursors and
-        // the geometry
+        // ids, the own precursor record and the geometry (no dependent level)
         int code[3];
-        R Io[3], gn[3][3], kap = R(0);
+        R gn[3][3], kap = R(0);
         if (!all) {
-            const unsigned nbfc = M.nbf[c];
 #pragma unroll
             for (int f = 0; f < 3; ++f) code[f] = M.nbr[f * ld + c];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const int nf = (nbfc >> (2 * f)) & 3;
-                Io[f] = (code[f] >= 0) ? __ldg(kx + (size_t)code[f] * KX_COUNT + KX_I0 + nf) : R(0);
-            }
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 gn[f][0] = M.geo[(G_N0X + 3 * f) * ld + c];
@@ -988,7 +981,7 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
             }
             kap = M.geo[G_KAPPA * ld + c];
         }
-        R k8[KX_COUNT];
+        R k8[KX_STRIDE];  // own precursors and, at KX_O0 + f, the neighbours' face means
         load_kx<R>(kx, c, k8);
         R vx, vy;
         if (EQ == EULER) {
@@ -1019,7 +1012,7 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
                 const R nl = gn[f][2];
                 R J;
                 if (code[f] >= 0) {
-                    J = k8[KX_I0 + f] - Io[f];
+                    J = k8[KX_I0 + f] - k8[KX_O0 + f];
                 } else {
                     const BFace bf = M.bf[-code[f] - 1];
                     const int kind = M.bc->kind[bf.tag];

@@ -217,6 +217,15 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
 #pragma unroll
             for (int v = 0; v < NV; ++v) k8[KX_M0 + v] = res[v][0];
             store_kx<R>(kx, c, k8);
+            // this cell's face means also go to the neighbours' records, at the
+            // slot of the shared face, so that the detection reads no neighbour
+            const int ld = M.ldc;
+            const unsigned nbfc = M.nbf[c];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int code = M.nbr[f * ld + c];
+                if (code >= 0) kx[(size_t)code * KX_STRIDE + KX_O0 + ((nbfc >> (2 * f)) & 3)] = k8[KX_I0 + f];
+            }
         }
     }
     // last stage of a step: the largest wave speed of the new means, for the next

@@ -1,0 +1,72 @@
+"""Edge cases on the GPU: the smallest meshes (2 and 8 cells on a periodic
+square, where every neighbour of a cell is the same cell across different
+faces; 2 cells with transmissive boundaries), and argument errors that the C
+interface must report as statuses."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_06280_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (1, 2), (2, 1), (2, 2)])
+def test_tiny_periodic_burgers_fp64(csw, cuda_stream, n, k):
+    pb = W.burgers_sine(n, seed=11)
+    s = csw.Solver(0, k, csw.FP64, csw.LIMITER_ALL, stream=cuda_stream)
+    s.setup(pb)
+    o = oracle.Oracle(pb, k=k, limiter=2)
+    u = o.project(pb.u0)
+    ug, fg = s.limit(u, 0.0)
+    uo, fo, st = o.limit(u, 0.0)
+    assert st == 0 and np.array_equal(fg, fo)
+    assert rel(ug, uo) < 1e-11
+    dt = 0.5 * o.cfl_dt(u, 0.1)
+    for i in range(3):
+        u, _, st = o.step(u, i * dt, dt)
+    s.write_modes(o.project(pb.u0))
+    s.set_time(0.0)
+    s.step(dt, 3, 1e9)
+    assert rel(s.read_modes(), u) < 1e-11
+
+
+def test_two_cell_euler_transmissive_fp64(csw, cuda_stream):
+    pb = W.riemann_quadrants(1, seed=14)
+    assert pb.mesh.nc == 2
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    u = W.random_modes(pb.mesh, 4, 6, 5)
+    assert rel(s.eval_rhs(u, 0.0), o.rhs(u, 0.0)) < 1e-11
+    ug, fg = s.limit(u, 0.0)
+    uo, fo, st = o.limit(u, 0.0)
+    assert st == 0 and np.array_equal(fg, fo)
+    assert rel(ug, uo) < 1e-11
+
+
+def test_argument_errors_are_statuses(csw, cuda_stream):
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.step(0.0, 1, 1.0)  # no mesh yet
+    pb = W.riemann_quadrants(3, seed=14)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.mesh_upload(pb.mesh.xy, pb.mesh.tri[:0], pb.mesh.bface, None)  # no triangles
+    s.setup(pb)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.step(0.0, -1, 1.0)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.set_stage_shape(100, 0)
+    u = W.random_modes(pb.mesh, 4, 6, 6)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.adjoint_steps(u, u, 0.0, 1, 1)
+    s.close()
+    s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_OFF, stream=cuda_stream)
+    s.setup(pb)
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.limit_adjoint(u, u, 0.0)
+    s.close()
