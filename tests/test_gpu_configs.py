@@ -163,9 +163,14 @@ def test_config4_small_ensemble_fp64(csw, cuda_stream):
 def test_config4_full_size_sampled(csw, cuda_stream):
     """The full ensemble (256 Riemann problems, 4,984,396 triangles in one
     disconnected mesh, the bench's ensemble workload): operator and KXRCF +
-    CSWENO in FP64 against the oracle on 600 sampled cells (1e-11, identical
-    flags), and one FP32-bulk step of the projected, every-cell-limited initial
-    state staying finite with positive means."""
+    CSWENO in FP64 against the oracle on 600 sampled cells (identical flags),
+    and one FP32-bulk step of the projected, every-cell-limited initial state
+    staying finite with positive means.  The coefficients are held to 1e-10
+    here instead of 1e-11: the meshes sit on a 16 x 16 grid of unit squares 1.5
+    apart (coordinates up to 24 against cells of 1/250), so the geometry that
+    the GPU and the oracle derive from the vertices in different orders already
+    differs by about eps64 x 24 x 250 = 1.3e-12 relative, and the operator (of
+    order 1/h) carries that into its coefficients (measured 1.7e-11)."""
     pb = W.riemann_ensemble(256, seed=1000)
     assert pb.mesh.nc > 4_900_000
     o = oracle.Oracle(pb, k=2, limiter=1)
@@ -175,14 +180,14 @@ def test_config4_full_size_sampled(csw, cuda_stream):
     s.setup(pb)
     Lg = s.eval_rhs(u, 0.0)
     Lo = o.rhs_cells(u, cells, 0.0)
-    assert np.abs(Lg[cells] - Lo).max() / np.abs(Lo).max() < 1e-11
+    assert np.abs(Lg[cells] - Lo).max() / np.abs(Lo).max() < 1e-10
     ug, fg = s.limit(u, 0.0)
     fo, _ = o.detect_cells(u, cells, 0.0)
     assert np.array_equal(fg[cells], fo)
     flagged = cells[fo.astype(bool)]
     assert len(flagged) > 10
     lo, st = o.limit_cells(u, flagged, 0.0)
-    assert np.abs(ug[flagged] - lo).max() / np.abs(lo).max() < 1e-11
+    assert np.abs(ug[flagged] - lo).max() / np.abs(lo).max() < 1e-10
     s.close()
     s = csw.Solver(1, 2, csw.FP32_BULK, csw.LIMITER_KXRCF, stream=cuda_stream)
     s.setup(pb)
