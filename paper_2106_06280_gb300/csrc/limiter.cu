@@ -588,7 +588,7 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
                 e[f] = b1[f] + W(eps);
             }
             const W d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
-            const W D = (d01 * d01 + d12 * d12 + d20 * d20) / 3.0;
+            const W D = (d01 * d01 + d12 * d12 + d20 * d20) * W(1.0 / 3.0);  // a product: a double division is slow on this FP64 pipe
             const W D2 = D * D;
             // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
             const W w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
