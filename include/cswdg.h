@@ -166,8 +166,8 @@ cswdg_status cswdg_rhs_adjoint(cswdg_solver *s, double t, const double *modes_in
 cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_in, const double *lambda_in, double *grad_out,
                                  uint8_t *flags_out);
 
-/* Hand-written adjoint of nsteps fixed-dt SSP-RK3 steps (Sec. 4, Table tvd)
- * with the limiter after every stage (Sec. 3): runs the steps forward from
+/* Hand-written adjoint of nsteps SSP-RK3 steps (Sec. 4, Table tvd) with the
+ * limiter after every stage (Sec. 3): runs the steps forward from
  * u0_user, keeping the state every checkpoint_every steps, then sweeps back:
  * each segment is recomputed stage by stage from its checkpoint (keeping the
  * unlimited stage outputs and the troubled-cell lists), and the transposed
@@ -175,15 +175,19 @@ cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_
  * and the limiter adjoint of cswdg_limit_adjoint (flags frozen as the forward
  * run set them, derivatives through the WENO weights).  Returns in g0_user
  * the gradient (du_N/du_0)^T gT_user, and in uT_user (nullable) the final
- * state u_N.  dt is held fixed (the CFL choice of dt is not differentiated);
- * the every-cell limiter is treated like KXRCF with every cell flagged.  Host
+ * state u_N.  dt > 0: every step has size dt; dt <= 0: the forward sweep
+ * takes the CFL rule of cswdg_step at every step and the reverse sweep holds
+ * the sizes it chose fixed (the dependence of dt on the state is not
+ * differentiated); dt_host (nullable, nsteps doubles) receives the sizes.
+ * The every-cell limiter is treated like KXRCF with every cell flagged.  Host
  * arrays: nc*nvar*np doubles, user basis and cell order.  Device work
  * memory: about (nsteps/checkpoint_every + 6 checkpoint_every + 5) state
  * arrays and 3 checkpoint_every cell lists, allocated and freed inside the
- * call.  Leaves the solver at u_N and t + nsteps dt.
- * Errors: EINVAL, ENONPHYS, ENOMEM, ECUDA. */
+ * call.  Leaves the solver at u_N and t plus the sum of the step sizes.
+ * Errors: EINVAL, ENONPHYS (also a CFL step of no positive size), ENOMEM,
+ * ECUDA. */
 cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int32_t checkpoint_every, const double *u0_user,
-                                 const double *gT_user, double *uT_user, double *g0_user);
+                                 const double *gT_user, double *uT_user, double *g0_user, double *dt_host);
 
 /* Launch-shape autotuner for the stage kernel (operator + RK update; no
  * counterpart in the paper).  Times CSWDG_TUNE_CANDIDATES shapes -- cells per

@@ -6,7 +6,9 @@ cell order) by nsteps fixed-dt SSP-RK3 steps with the solver's kernels and
 returns u_N; its backward pass calls ``cswdg_adjoint_steps``, which reruns
 the steps from u0 with checkpoints and sweeps back through the transposed
 stage updates (operator and limiter, troubled-cell flags frozen as the
-forward run set them) on the GPU.  The time step is held fixed (not
+forward run set them) on the GPU.  dt > 0 is a fixed step size; dt <= 0
+takes the CFL rule at every step, and the backward pass holds the step
+sizes of that forward run fixed (their dependence on the state is not
 differentiated).
 
 ``box_density_energy(uN, centroids, box)`` is the objective J of the

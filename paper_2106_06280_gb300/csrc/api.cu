@@ -953,10 +953,13 @@ cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_
 //   g0 += b1 + dt L'(u0)^T b1
 // ---------------------------------------------------------------------------
 cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int32_t checkpoint_every, const double *u0_user,
-                                 const double *gT_user, double *uT_user, double *g0_user)
+                                 const double *gT_user, double *uT_user, double *g0_user, double *dt_host)
 {
-    if (!s || !s->mesh_ready || !(dt > 0.0) || nsteps < 1 || checkpoint_every < 1 || !u0_user || !gT_user || !g0_user)
+    if (!s || !s->mesh_ready || nsteps < 1 || checkpoint_every < 1 || !u0_user || !gT_user || !g0_user)
         return fail(s, CSWDG_EINVAL, "adjoint_steps: bad arguments");
+    // dt <= 0: every step of the forward sweep takes the CFL rule; the sizes it
+    // chose are then held fixed in the recomputation and the reverse sweep
+    const int use_cfl = !(dt > 0.0);
     const bool lim = s->cfg.limiter != CSWDG_LIMITER_OFF;
     const size_t rs = s->fp32 ? 4 : 8, nstate = (size_t)s->nv * s->np * s->ldc, bytes = nstate * rs;
     const size_t flbytes = (size_t)s->ldc * 4;
@@ -970,8 +973,10 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
     const int grid = nsm * 4;
     char *ck = nullptr, *seg = nullptr, *ga = nullptr, *gw = nullptr, *gt = nullptr, *gx = nullptr, *uN = nullptr;
     int32_t *fls = nullptr, *nfs = nullptr;
+    double *dts = nullptr;
     cudaError_t e = cudaSuccess;
     auto A_ = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A_(cudaMalloc((void **)&dts, (size_t)nsteps * sizeof(double)));
     A_(cudaMalloc((void **)&ck, (size_t)nck * bytes));
     A_(cudaMalloc((void **)&seg, (size_t)NS * ce * bytes));
     A_(cudaMalloc((void **)&ga, bytes));
@@ -985,7 +990,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
     }
     auto release = [&]() {
         cudaFree(ck); cudaFree(seg); cudaFree(ga); cudaFree(gw); cudaFree(gt); cudaFree(gx); cudaFree(uN);
-        cudaFree(fls); cudaFree(nfs);
+        cudaFree(fls); cudaFree(nfs); cudaFree(dts);
     };
     if (e != cudaSuccess) {
         release();
@@ -1003,25 +1008,35 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
     } while (0)
     Ctl h;
     STR(read_ctl(s, &h));
-    // the step times exactly as k_begin_step accumulates them
-    std::vector<double> times((size_t)nsteps + 1);
-    times[0] = h.t_next;
-    for (int64_t n = 0; n < nsteps; ++n) times[n + 1] = times[n] + dt;
+    const double t0 = h.t_next;
     h.dt_fixed = dt;
+    h.cfl = s->cfg.cfl;
     h.t_end = 1e300;
     STR(upload_modes(s, u0_user, s->U));
     s->lam_stale = true;
+    if (use_cfl) STR(refresh_lam(s, &h, nullptr));
     STR(write_ctl(s, &h));
-    STR(get_graph(s, 0));
-    // forward sweep, checkpoints of u^n every ce steps
+    STR(get_graph(s, use_cfl));
+    // forward sweep, checkpoints of u^n every ce steps and the step sizes taken
     for (int64_t n = 0; n < nsteps; ++n) {
         if (n % ce == 0) CKR(cudaMemcpyAsync(ck + (size_t)(n / ce) * bytes, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
-        CKR(cudaGraphLaunch(s->graph[0], s->stream));
+        CKR(cudaGraphLaunch(s->graph[use_cfl], s->stream));
+        CKR(cudaMemcpyAsync(dts + n, &s->ctl->dt, sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     }
     CKR(cudaMemcpyAsync(uN, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
+    std::vector<double> dtv((size_t)nsteps);
+    CKR(cudaMemcpyAsync(dtv.data(), dts, (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     Ctl hf;
     STR(read_ctl(s, &hf));
     if (cswdg_status r = check_err(s, &hf)) { release(); return r; }
+    // the step times exactly as k_begin_step accumulated them
+    std::vector<double> times((size_t)nsteps + 1);
+    times[0] = t0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (!(dtv[n] > 0.0)) { release(); return fail(s, CSWDG_ENONPHYS, "adjoint_steps: step %lld has no positive size", (long long)n); }
+        times[n + 1] = times[n] + dtv[n];
+    }
+    if (dt_host) std::copy(dtv.begin(), dtv.end(), dt_host);
     if (uT_user) STR(download_modes(s, s->U, uT_user));
     // reverse sweep
     STR(upload_modes(s, gT_user, ga, true));
@@ -1035,7 +1050,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
             Ctl ws = hf;
             ws.t = times[n];
-            ws.dt = dt;
+            ws.dt = dtv[n];
             ws.active = 1;
             STR(write_ctl(s, &ws));
             CKR(cudaMemcpyAsync(base, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
@@ -1060,7 +1075,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             const int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
             Ctl ws = hf;
             ws.t = times[n];
-            ws.dt = dt;
+            ws.dt = dtv[n];
             ws.active = 1;
             STR(write_ctl(s, &ws));
             const void *u0s = base, *v1 = base + bytes, *v2 = base + 2 * bytes, *v3 = base + 3 * bytes, *u1s = base + 4 * bytes,
@@ -1068,7 +1083,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             auto run = [&](auto tag) {
                 using R = decltype(tag);
                 const MeshDev<R> M = mesh_dev<R>(s);
-                const R d = (R)dt;
+                const R d = (R)dtv[n];
                 R *a = (R *)ga, *wv = (R *)gw, *tv = (R *)gt, *xv = (R *)gx;
                 if (lim) {  // b3 = Lam_3'^T g
                     limit_adjoint_dev<R>(s, v3, fl + 2 * (size_t)s->ldc, nf + 2, 1.0, a, xv, nstate, s->stream);

@@ -67,7 +67,7 @@ def _load():
         "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
         "cswdg_autotune": ([vp, dp, C.POINTER(i32)], C.c_int),
         "cswdg_rhs_adjoint": ([vp, C.c_double, dp, dp, dp], C.c_int),
-        "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp], C.c_int),
+        "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp, dp], C.c_int),
         "cswdg_limit_adjoint": ([vp, C.c_double, dp, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
         "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
     }
@@ -234,13 +234,16 @@ class Solver:
         self._chk(lib.cswdg_rhs_adjoint(self.h, t, _p(modes), _p(lam), _p(out)))
         return out
 
-    def adjoint_steps(self, u0, gT, dt, nsteps, checkpoint_every=20):
-        """Run nsteps fixed-dt steps from u0 and return (u_N, (du_N/du_0)^T gT)."""
+    def adjoint_steps(self, u0, gT, dt, nsteps, checkpoint_every=20, return_dts=False):
+        """Run nsteps steps from u0 (size dt, or the CFL rule when dt <= 0, the
+        sizes then held fixed backwards) and return (u_N, (du_N/du_0)^T gT),
+        plus the step sizes when return_dts."""
         u0, gT = _d(u0), _d(gT)
         uT = np.zeros_like(u0)
         g0 = np.zeros_like(u0)
-        self._chk(lib.cswdg_adjoint_steps(self.h, dt, nsteps, checkpoint_every, _p(u0), _p(gT), _p(uT), _p(g0)))
-        return uT, g0
+        dts = np.zeros(int(nsteps))
+        self._chk(lib.cswdg_adjoint_steps(self.h, dt, nsteps, checkpoint_every, _p(u0), _p(gT), _p(uT), _p(g0), _p(dts)))
+        return (uT, g0, dts) if return_dts else (uT, g0)
 
     def limit_adjoint(self, modes, lam, t=0.0):
         """(dLim/du)^T lam at the state modes with the flags frozen; returns (grad, flags)."""

@@ -63,7 +63,7 @@ def test_argument_errors_are_statuses(csw, cuda_stream):
         s.set_stage_shape(100, 0)
     u = W.random_modes(pb.mesh, 4, 6, 6)
     with pytest.raises(csw.CswdgError, match="EINVAL"):
-        s.adjoint_steps(u, u, 0.0, 1, 1)
+        s.adjoint_steps(u, u, 0.1, 1, 0)  # no checkpoint interval
     s.close()
     s = csw.Solver(1, 2, csw.FP64, csw.LIMITER_OFF, stream=cuda_stream)
     s.setup(pb)
