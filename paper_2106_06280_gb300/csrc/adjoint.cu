@@ -7,9 +7,11 @@
 // Owner-computes, one thread per cell, no atomics: cell c collects every term
 // of sum_d lambda_d . L_d that depends on its own coefficients -- its volume
 // integral, and at each of its faces the flux in its own residual and in the
-// neighbour's residual (the same canonical flux value, see the stage kernel).
-// Where the forward flux takes a maximum (the local Lax-Friedrichs speed) the
-// derivative follows the branch the forward evaluation takes.
+// neighbour's residual (one flux value: the two cells of a face evaluate exact
+// negatives of each other, see llf2).  Here each face is differentiated in the
+// orientation of its lower-index cell.  Where the flux takes a maximum (the
+// local Lax-Friedrichs speed) the derivative follows the larger side, as the
+// forward evaluation does (at an exact tie either side is a valid choice).
 #include "kernels.h"
 #include "physics.cuh"
 #include "tables.cuh"

@@ -97,6 +97,8 @@ template <typename R, int K> struct Tab {
     R fw[Deg<K>::QF];                 // face weights (sum 1)
     R ft[Deg<K>::QF];                 // Gauss points as edge parameters in [0,1]
     R fint[3][Deg<K>::NP];            // sum_g fw[g] psi_m(point g of face f): the face mean of psi_m
+    R vdrw[Deg<K>::QV][Deg<K>::NP];   // vw[q] d psi_m / dr (weight folded in, rounded once)
+    R vdsw[Deg<K>::QV][Deg<K>::NP];   // vw[q] d psi_m / ds
 };
 
 // Traces seen from the neighbour: psi_m at the Gauss points of local face nf

@@ -961,28 +961,30 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
                                                    int all, uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
 {
     constexpr int QF = Deg<K>::QF;
-    if (!ctl->active) return;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     int flag = 0;
-    if (c < M.nc) {
-        const int ld = M.ldc;
-        // every load of the thread is issued before the first use: the neighbour
-        // ids, the own precursor record and the geometry (no dependent level)
-        int code[3];
-        R gn[3][3], kap = R(0);
-        if (!all) {
+    // every load of the thread is issued before the first use, and before the
+    // read of the step's active flag: the neighbour ids, the geometry and the
+    // own precursor record with the neighbours' face means (no load depends on
+    // another)
+    int code[3] = {0, 0, 0};
+    R gn[3][3] = {}, kap = R(0);
+    R k8[KX_STRIDE] = {};
+    const int ld = M.ldc;
+    if (c < M.nc && !all) {
 #pragma unroll
-            for (int f = 0; f < 3; ++f) code[f] = M.nbr[f * ld + c];
+        for (int f = 0; f < 3; ++f) code[f] = M.nbr[f * ld + c];
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                gn[f][0] = M.geo[(G_N0X + 3 * f) * ld + c];
-                gn[f][1] = M.geo[(G_N0Y + 3 * f) * ld + c];
-                gn[f][2] = M.geo[(G_N0L + 3 * f) * ld + c];
-            }
-            kap = M.geo[G_KAPPA * ld + c];
+        for (int f = 0; f < 3; ++f) {
+            gn[f][0] = M.geo[(G_N0X + 3 * f) * ld + c];
+            gn[f][1] = M.geo[(G_N0Y + 3 * f) * ld + c];
+            gn[f][2] = M.geo[(G_N0L + 3 * f) * ld + c];
         }
-        R k8[KX_STRIDE];  // own precursors and, at KX_O0 + f, the neighbours' face means
-        load_kx<R>(kx, c, k8);
+        kap = M.geo[G_KAPPA * ld + c];
+    }
+    if (c < M.nc) load_kx<R>(kx, c, k8);
+    if (!ctl->active) return;
+    if (c < M.nc) {
         R vx, vy;
         if (EQ == EULER) {
             const R r = k8[KX_M0], mx = k8[KX_M1], my = k8[KX_M2], E = k8[KX_M3];

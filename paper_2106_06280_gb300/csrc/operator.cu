@@ -77,6 +77,38 @@ template <typename R> __device__ __forceinline__ void block_max_to_ctl(R lam, Ct
     }
 }
 
+// trace of the modes a at one point: the mean's share a0 (= a[v][0] psi_0) plus
+// the higher modes in a fixed fused order, so that a cell's own trace and the
+// same trace formed by its neighbour are equal bit for bit
+template <int NV, int NP, typename R>
+__device__ __forceinline__ void trace(const R (&a0)[NV], const R (&a)[NV][NP], const R *__restrict__ phi, R (&U)[NV])
+{
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        R sv = a0[v];
+#pragma unroll
+        for (int m = 1; m < NP; ++m) sv = rfma(a[v][m], phi[m], sv);
+        U[v] = sv;
+    }
+}
+
+// one face point: twice the LLF flux between this cell's trace Ui (first) and
+// the other side's Uo, through this cell's outward normal, weighted by
+// wgt = w_g |n~| / 2 and taken off the residual against psi_i at the point
+template <int EQ, int NV, int NP, typename R>
+__device__ __forceinline__ void face_point(const R (&Ui)[NV], const R (&Uo)[NV], R nx, R ny, R gam, R wgt,
+                                           const R *__restrict__ phi, R (&acc)[NV][NP])
+{
+    R F[NV];
+    llf2<EQ, R>(Ui, Uo, nx, ny, gam, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const R wf = wgt * F[v];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) acc[v][m] -= phi[m] * wf;
+    }
+}
+
 // Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
 // One thread per cell; each cell evaluates its volume integral and all three
 // face integrals (the neighbour's trace is read from its modes), so no face
@@ -100,83 +132,64 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
 #pragma unroll
         for (int m = 0; m < NP; ++m) acc[v][m] = R(0);
     const R g0 = M.geo[G_RX * ld + c], g1 = M.geo[G_RY * ld + c], g2 = M.geo[G_SX * ld + c], g3 = M.geo[G_SY * ld + c];
+    // psi_0 is the same constant at every point: the mean's share of a trace is
+    // formed once per cell (and once per neighbour), and every trace sum starts from it
+    const R psi0 = T.vphi[0][0];
+    R m0[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) m0[v] = u[v][0] * psi0;
 
     // volume integral
 #pragma unroll
     for (int q = 0; q < QV; ++q) {
         R U[NV], f[NV], g[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            R sv = R(0);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) sv += u[v][m] * T.vphi[q][m];
-            U[v] = sv;
-        }
+        trace<NV, NP, R>(m0, u, T.vphi[q], U);
         flux_fg<EQ, R>(U, gam, f, g);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const R Fr = T.vw[q] * (g0 * f[v] + g1 * g[v]);
-            const R Fs = T.vw[q] * (g2 * f[v] + g3 * g[v]);
+            const R Fr = g0 * f[v] + g1 * g[v];
+            const R Fs = g2 * f[v] + g3 * g[v];
             // psi_0 is constant and psi_1..psi_K (Jacobi index i = 0) do not depend on r:
-            // their derivative terms are exact zeros and are skipped
+            // their derivative terms are exact zeros and are skipped; the volume
+            // weight is folded into the derivative tables
 #pragma unroll
-            for (int m = 1; m < NP; ++m) acc[v][m] += (m > K) ? T.vdr[q][m] * Fr + T.vds[q][m] * Fs : T.vds[q][m] * Fs;
+            for (int m = 1; m < NP; ++m) acc[v][m] += (m > K) ? T.vdrw[q][m] * Fr + T.vdsw[q][m] * Fs : T.vdsw[q][m] * Fs;
         }
     }
 
-    // face integrals: -|n~| sum_g w_g psi_i F*(u-, u+; n), n the outward unit normal
+    // face integrals: -|n~| sum_g w_g psi_i F*(u-, u+; n), n this cell's outward unit
+    // normal; llf2 returns 2 F*, so the face factor carries 1/2 |n~|
     const unsigned nbf = M.nbf[c];
-    // faces and their Gauss points are not unrolled: the fully unrolled body
-    // ran slower (instruction-cache misses and register pressure)
+    // the face loop is not unrolled (the fully unrolled body ran slower:
+    // instruction-cache misses and register pressure); its Gauss points are
 #pragma unroll 1
     for (int f = 0; f < 3; ++f) {
-        const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c], nl = M.geo[(G_N0L + 3 * f) * ld + c];
+        const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c];
+        const R hnl = R(0.5) * M.geo[(G_N0L + 3 * f) * ld + c];
         const int code = M.nbr[f * ld + c];
-        R w[NV][NP];
-        const int nf = (nbf >> (2 * f)) & 3;
-        const bool swap = code >= 0 && code < c;
-        const R snl = swap ? -nl : nl;
-        BFace bf;
-        if (code >= 0) load_cell<NV, NP>(up, code, w);
-        else bf = M.bf[-code - 1];
-#pragma unroll 1
-        for (int g = 0; g < QF; ++g) {
-            R Ui[NV], Uo[NV], F[NV];
+        if (code >= 0) {
+            // interior face: the neighbour's trace from its modes, at the reversed
+            // point of its local face nf
+            const int nf = (nbf >> (2 * f)) & 3;
+            R w[NV][NP], w0[NV];
+            load_cell<NV, NP>(up, code, w);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                R sv = R(0);
+            for (int v = 0; v < NV; ++v) w0[v] = w[v][0] * psi0;
 #pragma unroll
-                for (int m = 0; m < NP; ++m) sv += u[v][m] * T.fphi[f][g][m];
-                Ui[v] = sv;
+            for (int g = 0; g < QF; ++g) {
+                R Ui[NV], Uo[NV];
+                trace<NV, NP, R>(m0, u, T.fphi[f][g], Ui);
+                trace<NV, NP, R>(w0, w, T.fphi[nf][QF - 1 - g], Uo);
+                face_point<EQ, NV, NP, R>(Ui, Uo, nx, ny, gam, T.fw[g] * hnl, T.fphi[f][g], acc);
             }
-            if (code >= 0) {
+        } else {
+            const BFace bf = M.bf[-code - 1];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    R sv = R(0);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) sv += w[v][m] * T.fphi[nf][QF - 1 - g][m];
-                    Uo[v] = sv;
-                }
-            } else {
+            for (int g = 0; g < QF; ++g) {
+                R Ui[NV], Uo[NV];
+                trace<NV, NP, R>(m0, u, T.fphi[f][g], Ui);
                 ghost<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), Ui, Uo);
-            }
-            // both cells of a face evaluate the flux in the same canonical order (the
-            // lower internal index as the left state), so their two values are exact
-            // negatives and the cell means are conserved to the rounding of the update
-            {
-                R A[NV], B[NV];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    A[v] = swap ? Uo[v] : Ui[v];
-                    B[v] = swap ? Ui[v] : Uo[v];
-                }
-                llf<EQ, R>(A, B, swap ? -nx : nx, swap ? -ny : ny, R(1), gam, F);
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const R wf = T.fw[g] * snl * F[v];
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[v][m] -= T.fphi[f][g][m] * wf;
+                face_point<EQ, NV, NP, R>(Ui, Uo, nx, ny, gam, T.fw[g] * hnl, T.fphi[f][g], acc);
             }
         }
     }
@@ -231,10 +244,10 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
     // last stage of a step: the largest wave speed of the new means, for the next
     // step's CFL rule (the reconstruction that follows keeps every cell mean)
     if (!lam_next) return R(0);
-    R m0[NV];
+    R mn[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) m0[v] = res[v][0];
-    return mean_wave_speed<EQ, R>(m0, gam);
+    for (int v = 0; v < NV; ++v) mn[v] = res[v][0];
+    return mean_wave_speed<EQ, R>(mn, gam);
 }
 
 // Stage kernel: tiles of BLK consecutive cells (Morton order), one thread per

@@ -36,6 +36,35 @@ __host__ __device__ __forceinline__ float rsqrt_fast(float x)
 #endif
 }
 
+// reciprocal and square root of the stage kernel's fluxes: IEEE in FP64; in
+// float the single-instruction approximations rcp.approx and sqrt.approx of
+// the PTX ISA (sqrt.approx gives 0 at 0 and a NaN below it)
+__host__ __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__host__ __device__ __forceinline__ float frcp(float x)
+{
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return 1.0f / x;
+#endif
+}
+__host__ __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+__host__ __device__ __forceinline__ float fsqrt(float x)
+{
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return sqrtf(x);
+#endif
+}
+// explicitly rounded fused multiply-add (never re-associated or re-contracted)
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 // physical flux (f, g) at U
 template <int EQ, typename R> __host__ __device__ __forceinline__ void flux_fg(const R *U, R gam, R *f, R *g)
 {
@@ -44,7 +73,7 @@ template <int EQ, typename R> __host__ __device__ __forceinline__ void flux_fg(c
         f[0] = h;
         g[0] = h;
     } else {
-        const R ir = rrcp(U[0]);
+        const R ir = frcp(U[0]);
         const R u = U[1] * ir, v = U[2] * ir;
         const R p = (gam - R(1)) * (U[3] - R(0.5) * (U[1] * u + U[2] * v));
         f[0] = U[1]; f[1] = U[1] * u + p; f[2] = U[2] * u; f[3] = (U[3] + p) * u;
@@ -52,25 +81,43 @@ template <int EQ, typename R> __host__ __device__ __forceinline__ void flux_fg(c
     }
 }
 
-// local Lax-Friedrichs flux through a normal n of length nl (the stage kernel passes a unit normal):
-// F = 1/2 (F(UL) + F(UR)).n - 1/2 a (UR - UL), a = max |eigenvalue| along n
-template <int EQ, typename R> __host__ __device__ __forceinline__ void llf(const R *UL, const R *UR, R nx, R ny, R nl, R gam, R *F)
+// Twice the local Lax-Friedrichs flux (Sec. 2, the monotone flux f*, g*
+// taken pointwise with the local maximum wave speed) through the unit normal n:
+// 2F = (F(UL) + F(UR)).n - a (UR - UL), a = max |eigenvalue| along n.
+// Every per-side quantity is computed by the same explicitly rounded sequence
+// and the two sides meet only in commutative sums and in the maximum, so
+//   llf2(UR, UL, -n) = -llf2(UL, UR, n)   bit for bit:
+// the two cells of a face, each passing its own trace first and its own
+// outward normal (the exact negative of the neighbour's), obtain exact
+// negatives, and the cell means are conserved to the rounding of the update.
+template <int EQ, typename R> __device__ __forceinline__ void llf2_side(const R *U, R nx, R ny, R gm1, R gh, R gam, R *fn, R &s)
+{
+    const R ir = frcp(U[0]);
+    const R un = rmul_rn(rfma(U[1], nx, rmul_rn(U[2], ny)), ir);
+    const R ke = rmul_rn(rfma(U[1], U[1], rmul_rn(U[2], U[2])), ir);
+    const R p = rfma(-gh, ke, rmul_rn(gm1, U[3]));
+    s = radd_rn(fabs(un), fsqrt(rmul_rn(rmul_rn(gam, p), ir)));
+    fn[0] = rmul_rn(U[0], un);
+    fn[1] = rfma(U[1], un, rmul_rn(p, nx));
+    fn[2] = rfma(U[2], un, rmul_rn(p, ny));
+    fn[3] = rmul_rn(radd_rn(U[3], p), un);
+}
+
+template <int EQ, typename R> __device__ __forceinline__ void llf2(const R *UL, const R *UR, R nx, R ny, R gam, R *F)
 {
     if (EQ == BURGERS) {
-        const R s = nx + ny;
-        const R a = rmax(rabs(UL[0]), rabs(UR[0])) * rabs(s);
-        F[0] = R(0.25) * (UL[0] * UL[0] + UR[0] * UR[0]) * s - R(0.5) * a * (UR[0] - UL[0]);
+        const R sn = radd_rn(nx, ny);
+        const R a = rmul_rn(fmax(fabs(UL[0]), fabs(UR[0])), fabs(sn));
+        const R q = rmul_rn(R(0.5) * radd_rn(rmul_rn(UL[0], UL[0]), rmul_rn(UR[0], UR[0])), sn);
+        F[0] = rfma(-a, radd_rn(UR[0], -UL[0]), q);
     } else {
-        const R irl = rrcp(UL[0]), irr = rrcp(UR[0]);
-        const R unl = (UL[1] * nx + UL[2] * ny) * irl, unr = (UR[1] * nx + UR[2] * ny) * irr;
-        const R pl = (gam - R(1)) * (UL[3] - R(0.5) * (UL[1] * UL[1] + UL[2] * UL[2]) * irl);
-        const R pr = (gam - R(1)) * (UR[3] - R(0.5) * (UR[1] * UR[1] + UR[2] * UR[2]) * irr);
-        const R cl = rsqrt_fast(gam * pl * irl), cr = rsqrt_fast(gam * pr * irr);
-        const R a = rmax(rabs(unl) + cl * nl, rabs(unr) + cr * nl);
-        F[0] = R(0.5) * (UL[0] * unl + UR[0] * unr) - R(0.5) * a * (UR[0] - UL[0]);
-        F[1] = R(0.5) * (UL[1] * unl + pl * nx + UR[1] * unr + pr * nx) - R(0.5) * a * (UR[1] - UL[1]);
-        F[2] = R(0.5) * (UL[2] * unl + pl * ny + UR[2] * unr + pr * ny) - R(0.5) * a * (UR[2] - UL[2]);
-        F[3] = R(0.5) * ((UL[3] + pl) * unl + (UR[3] + pr) * unr) - R(0.5) * a * (UR[3] - UL[3]);
+        const R gm1 = gam - R(1), gh = R(0.5) * gm1;
+        R fl[4], fr[4], sl, sr;
+        llf2_side<EQ, R>(UL, nx, ny, gm1, gh, gam, fl, sl);
+        llf2_side<EQ, R>(UR, nx, ny, gm1, gh, gam, fr, sr);
+        const R a = fmax(sl, sr);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) F[v] = rfma(-a, radd_rn(UR[v], -UL[v]), radd_rn(fl[v], fr[v]));
     }
 }
 

@@ -40,6 +40,8 @@ template <typename R, int K> inline void make_tab(Tab<R, K> &T)
             T.vphi[q][m] = (R)v;
             T.vdr[q][m] = (R)dr;
             T.vds[q][m] = (R)ds;
+            T.vdrw[q][m] = (R)(vr.w[q] * dr);
+            T.vdsw[q][m] = (R)(vr.w[q] * ds);
         }
     }
     double t[4], w[4];
