@@ -84,13 +84,13 @@ def stage_bytes_per_cell(fp32: bool) -> float:
     averaged over the three stages: read u^(i-1) (S), write u^(i) (S), read u^n
     (S, stages 2 and 3), geometry (4 inverse-Jacobian + 9 scaled-normal words),
     three neighbour indices (12 B), the packed neighbour faces (1 B) and the
-    KXRCF precursors written for the detection (8 words in the cell's record,
+    KXRCF precursors written for the detection (7 words in the cell's record,
     3 face means into the neighbours' records).  Neighbour traces are reuse of
     data already counted."""
     s = 4 if fp32 else 8
     S = NP * NV * s
     geo = 13 * s + 12 + 1
-    kx = 11 * s
+    kx = 10 * s
     return (3 * (2 * S + geo + kx) + 2 * S) / 3.0
 
 

@@ -179,14 +179,16 @@ __device__ __forceinline__ double stage_time(const Ctl *ctl, double tfac)
 }
 
 // KXRCF precursors of a cell, written by the stage kernel for its new state
-// (8 words per cell): the face means of the indicator variable on the three
-// faces, the squared L2 coefficient norm of the indicator variable, and the
-// four (Burgers: one) mean coefficients.
-enum { KX_I0 = 0, KX_I1, KX_I2, KX_NRM2, KX_M0, KX_M1, KX_M2, KX_M3, KX_COUNT };
+// (7 words per cell): the face means of the indicator variable on the three
+// faces; per face the inflow weight (0 on an outflow face, where the mean
+// velocity has v.n >= 0; |n~| on an inflow face to a neighbour, -|n~| on an
+// inflow boundary face); the squared L2 coefficient norm of the indicator
+// variable.  The stage kernel also checks the new means (ERR_NONPHYS).
+enum { KX_I0 = 0, KX_I1, KX_I2, KX_W0, KX_W1, KX_W2, KX_NRM2, KX_COUNT };
 // a cell's record is KX_STRIDE words: its own KX_COUNT words, then at KX_O0 + f
 // the face mean that the neighbour across face f wrote for the shared face
 // (so that the detection reads one record per cell and no neighbour's)
-enum { KX_O0 = KX_COUNT, KX_STRIDE = 12 };
+enum { KX_O0 = KX_COUNT, KX_STRIDE = 10 };
 
 // geometry array indices (REAL, SoA with leading dimension ldc): 2 x inverse
 // Jacobian; per face the outward unit normal and |n~| = 2 |e| / |K|; KXRCF scale
@@ -288,25 +290,28 @@ __device__ __forceinline__ void store_cell(R *p, int c, const R (&u)[NV][NP])
 }
 
 // 8 KXRCF precursor words of cell c (32 or 64 bytes, vector stores / loads)
-template <typename R> __device__ __forceinline__ void store_kx(R *kx, int c, const R (&k8)[KX_COUNT])
+// records start at multiples of 40 (float) or 80 (double) bytes: 8-byte
+// aligned in float, 16-byte aligned in double
+template <typename R> __device__ __forceinline__ void store_kx(R *kx, int c, const R (&k)[KX_COUNT])
 {
     R *q = kx + (size_t)c * KX_STRIDE;
     if (sizeof(R) == 4) {
-        reinterpret_cast<float4 *>(q)[0] = make_float4((float)k8[0], (float)k8[1], (float)k8[2], (float)k8[3]);
-        reinterpret_cast<float4 *>(q)[1] = make_float4((float)k8[4], (float)k8[5], (float)k8[6], (float)k8[7]);
+#pragma unroll
+        for (int i = 0; i < KX_COUNT / 2; ++i) reinterpret_cast<float2 *>(q)[i] = make_float2((float)k[2 * i], (float)k[2 * i + 1]);
     } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) reinterpret_cast<double2 *>(q)[i] = make_double2((double)k8[2 * i], (double)k8[2 * i + 1]);
+        for (int i = 0; i < KX_COUNT / 2; ++i) reinterpret_cast<double2 *>(q)[i] = make_double2((double)k[2 * i], (double)k[2 * i + 1]);
     }
+    q[KX_COUNT - 1] = k[KX_COUNT - 1];
 }
 template <typename R> __device__ __forceinline__ void load_kx(const R *__restrict__ kx, int c, R (&k)[KX_STRIDE])
 {
     const R *q = kx + (size_t)c * KX_STRIDE;
     if (sizeof(R) == 4) {
 #pragma unroll
-        for (int i = 0; i < KX_STRIDE / 4; ++i) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(q) + i);
-            k[4 * i] = a.x; k[4 * i + 1] = a.y; k[4 * i + 2] = a.z; k[4 * i + 3] = a.w;
+        for (int i = 0; i < KX_STRIDE / 2; ++i) {
+            const float2 a = __ldg(reinterpret_cast<const float2 *>(q) + i);
+            k[2 * i] = a.x; k[2 * i + 1] = a.y;
         }
     } else {
 #pragma unroll

@@ -517,6 +517,24 @@ __host__ __device__ __forceinline__ W quad_form(const R *__restrict__ L, const R
 // ===========================================================================
 // CSWENO reconstruction of one scalar field (Sec. 3.2 Steps 1-5 / Steps 1-4)
 // t[f][i]: subcell means of slot f (thirds 0..2, halves 3..6), w0: cell mean.
+// Reciprocal of a positive weight sum in W precision.  In double: the hardware
+// seed rcp.approx.ftz.f64 (PTX ISA) refined by two Newton-Raphson steps for
+// 1/x, r <- r + r (1 - x r), each of which about doubles the number of correct
+// bits, so the result is within an ulp or two of 1/x (the IEEE division is a
+// long FP64 sequence on this GPU).  The weights it normalises need no more.
+__host__ __device__ __forceinline__ double wrcp(double x)
+{
+#ifdef __CUDA_ARCH__
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    r = fma(r, fma(-x, r, 1.0), r);
+    return fma(r, fma(-x, r, 1.0), r);
+#else
+    return 1.0 / x;
+#endif
+}
+__host__ __device__ __forceinline__ float wrcp(float x) { return rrcp(x); }
+
 // ===========================================================================
 // W: precision of the smoothness indicators, tau and the nonlinear weights
 // (double: FP64 and FP32-bulk modes; float: FP32 mode)
@@ -592,26 +610,26 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
             const W D2 = D * D;
             // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
             const W w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
-            const W inv = 1.0 / (w0 + w1 + w2);
+            const W inv = wrcp(w0 + w1 + w2);
             const W ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
             beta[0] = ab * ab + bb * bb;
         }
         // Step 4: tau and nonlinear weights, normalised over a common denominator
         if (K == 1) {
             const W e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
-            const W tau = (e1 * e1 + e2 * e2) / 4.0;
+            const W tau = (e1 * e1 + e2 * e2) * 0.25;
             const W a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
             const W w0 = (W)gm[0] * (a0 + tau) * a1 * a2, w1 = (W)gm[1] * (a1 + tau) * a0 * a2, w2 = (W)gm[2] * (a2 + tau) * a0 * a1;
-            const W inv = 1.0 / (w0 + w1 + w2);
+            const W inv = wrcp(w0 + w1 + w2);
             om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = W(0);
         } else {
             const W e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
-            const W tau = (e1 * e1 + e2 * e2 + e3 * e3) / 16.0;
+            const W tau = (e1 * e1 + e2 * e2 + e3 * e3) * 0.0625;
             const W a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
             const W p01 = a[0] * a[1], p23 = a[2] * a[3];
             const W w[4] = {(W)gm[3] * (a[0] + tau) * a[1] * p23, (W)gm[4] * (a[1] + tau) * a[0] * p23,
                             (W)gm[5] * (a[2] + tau) * p01 * a[3], (W)gm[6] * (a[3] + tau) * p01 * a[2]};
-            const W inv = 1.0 / (w[0] + w[1] + w[2] + w[3]);
+            const W inv = wrcp(w[0] + w[1] + w[2] + w[3]);
             for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
         }
     } else {
@@ -963,44 +981,17 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
     constexpr int QF = Deg<K>::QF;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     int flag = 0;
-    // every load of the thread is issued before the first use, and before the
-    // read of the step's active flag: the neighbour ids, the geometry and the
-    // own precursor record with the neighbours' face means (no load depends on
-    // another)
-    int code[3] = {0, 0, 0};
-    R gn[3][3] = {}, kap = R(0);
-    R k8[KX_STRIDE] = {};
+    // the cell's record (own face means, inflow weights and norm, the
+    // neighbours' face means) and kappa are loaded before the read of the step's
+    // active flag; no load depends on another
+    R k8[KX_STRIDE] = {}, kap = R(0);
     const int ld = M.ldc;
-    if (c < M.nc && !all) {
-#pragma unroll
-        for (int f = 0; f < 3; ++f) code[f] = M.nbr[f * ld + c];
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            gn[f][0] = M.geo[(G_N0X + 3 * f) * ld + c];
-            gn[f][1] = M.geo[(G_N0Y + 3 * f) * ld + c];
-            gn[f][2] = M.geo[(G_N0L + 3 * f) * ld + c];
-        }
-        kap = M.geo[G_KAPPA * ld + c];
+    if (c < M.nc) {
+        load_kx<R>(kx, c, k8);
+        if (!all) kap = M.geo[G_KAPPA * ld + c];
     }
-    if (c < M.nc) load_kx<R>(kx, c, k8);
     if (!ctl->active) return;
     if (c < M.nc) {
-        R vx, vy;
-        if (EQ == EULER) {
-            const R r = k8[KX_M0], mx = k8[KX_M1], my = k8[KX_M2], E = k8[KX_M3];
-            const R q = R(2) * E * r - (mx * mx + my * my);
-            bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
-            if (!ok && !(q != q)) {
-                const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
-                ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
-            }
-            if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
-            vx = mx;
-            vy = my;
-        } else {
-            vx = vy = k8[KX_M0];
-            if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
-        }
         if (all) {
             flag = 1;
         } else {
@@ -1008,15 +999,16 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
             R num = R(0), lsum = R(0);
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const R nx = gn[f][0], ny = gn[f][1];
-                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
-                if (!(vn < R(0))) continue;
-                const R nl = gn[f][2];
-                R J;
-                if (code[f] >= 0) {
+                const R w = k8[KX_W0 + f];
+                if (w == R(0)) continue;  // outflow face
+                R J, nl;
+                if (w > R(0)) {
+                    nl = w;
                     J = k8[KX_I0 + f] - k8[KX_O0 + f];
                 } else {
-                    const BFace bf = M.bf[-code[f] - 1];
+                    nl = -w;
+                    const int code = M.nbr[f * ld + c];
+                    const BFace bf = M.bf[-code - 1];
                     const int kind = M.bc->kind[bf.tag];
                     if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
                         R go = R(0);

@@ -118,7 +118,7 @@ __device__ __forceinline__ void face_point(const R (&Ui)[NV], const R (&Uo)[NV],
 // lam_next is set (else 0)
 template <int EQ, int K, typename R>
 __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl,
-                                        double tfac, int lam_next, R *__restrict__ kx, const Ctl *__restrict__ ctl, int c)
+                                        double tfac, int lam_next, R *__restrict__ kx, Ctl *__restrict__ ctl, int c)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
     const Tab<R, K> &T = tab<R, K>();
@@ -138,6 +138,13 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
     R m0[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) m0[v] = u[v][0] * psi0;
+
+    // the neighbour ids and the face normals are loaded with the cell's own data,
+    // so that a face waits only for its neighbour's modes (one round trip)
+    const int fc0 = M.nbr[c], fc1 = M.nbr[ld + c], fc2 = M.nbr[2 * ld + c];
+    R fg[9];  // (nx, ny, |n~|) of faces 0, 1, 2
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fg[i] = M.geo[(G_N0X + i) * ld + c];
 
     // volume integral
 #pragma unroll
@@ -164,9 +171,10 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
     // instruction-cache misses and register pressure); its Gauss points are
 #pragma unroll 1
     for (int f = 0; f < 3; ++f) {
-        const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c];
-        const R hnl = R(0.5) * M.geo[(G_N0L + 3 * f) * ld + c];
-        const int code = M.nbr[f * ld + c];
+        // selected, not indexed: an indexed register array would go to local memory
+        const R nx = (f == 0) ? fg[0] : (f == 1) ? fg[3] : fg[6], ny = (f == 0) ? fg[1] : (f == 1) ? fg[4] : fg[7];
+        const R hnl = R(0.5) * ((f == 0) ? fg[2] : (f == 1) ? fg[5] : fg[8]);
+        const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
         if (code >= 0) {
             // interior face: the neighbour's trace from its modes, at the reversed
             // point of its local face nf
@@ -213,31 +221,52 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
         store_cell<NV, NP>(out, c, res);
         // KXRCF precursors of the new state for the detection that follows
         if (kx) {
-            R k8[KX_COUNT];
+            R k7[KX_COUNT];
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 R s = R(0);
 #pragma unroll
                 for (int m = 0; m < NP; ++m) s += res[0][m] * T.fint[f][m];
-                k8[KX_I0 + f] = s;
+                k7[KX_I0 + f] = s;
             }
             R n2 = R(0);
 #pragma unroll
             for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
-            k8[KX_NRM2] = n2;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) k8[KX_M0 + v] = R(0);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) k8[KX_M0 + v] = res[v][0];
-            store_kx<R>(kx, c, k8);
-            // this cell's face means also go to the neighbours' records, at the
-            // slot of the shared face, so that the detection reads no neighbour
-            const int ld = M.ldc;
-            const unsigned nbfc = M.nbf[c];
+            k7[KX_NRM2] = n2;
+            // the new means: physically admissible (Euler: rho > 0, p > 0; screened
+            // in the state precision, close calls in double), and the mean velocity
+            // direction (the momentum) that decides the inflow faces
+            R vx, vy;
+            if (EQ == EULER) {
+                const R r = res[0][0], mx = res[1][0], my = res[2][0], E = res[NV - 1][0];
+                const R q = R(2) * E * r - (mx * mx + my * my);
+                bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
+                if (!ok && !(q != q)) {
+                    const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
+                    ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
+                }
+                if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
+                vx = mx;
+                vy = my;
+            } else {
+                vx = vy = res[0][0];
+                if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+            }
+            // inflow weights: v.n < 0 (uncontracted, as a plain evaluation decides it)
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
-                const int code = M.nbr[f * ld + c];
-                if (code >= 0) kx[(size_t)code * KX_STRIDE + KX_O0 + ((nbfc >> (2 * f)) & 3)] = k8[KX_I0 + f];
+                const R nx = fg[3 * f], ny = fg[3 * f + 1], nl = fg[3 * f + 2];
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
+                k7[KX_W0 + f] = (vn < R(0)) ? ((code >= 0) ? nl : -nl) : R(0);
+            }
+            store_kx<R>(kx, c, k7);
+            // this cell's face means also go to the neighbours' records, at the
+            // slot of the shared face, so that the detection reads no neighbour
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                if (code >= 0) kx[(size_t)code * KX_STRIDE + KX_O0 + ((nbf >> (2 * f)) & 3)] = k7[KX_I0 + f];
             }
         }
     }
