@@ -412,27 +412,30 @@ template void launch_project<double>(int, int, int, int, const double *, double 
 // internal [(c*nv + v)*np + m], scaled by sc[c] = sqrt(2/|K|); perm[c] = user index.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_from_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm, const double *__restrict__ sc,
-                            const double *__restrict__ user, R *__restrict__ u)
+__global__ void __launch_bounds__(256) k_from_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm,
+                                                   const double *__restrict__ sc, const double *__restrict__ user, R *__restrict__ u)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    const size_t uc = (size_t)perm[c];
-    const double s = sc[c];
-    for (int v = 0; v < nv; ++v)
-        for (int m = 0; m < np; ++m) u[sidx(nv, np, v, m, c)] = (R)(s * user[(uc * nv + v) * np + m]);
+    // one thread per coefficient: a warp covers consecutive coefficients of one
+    // or two cells, so the reads of the cell's user row and the writes of its
+    // internal row are both contiguous
+    const int npv = nv * np;
+    const size_t n = (size_t)nc * npv;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / npv), j = (int)(e - (size_t)c * npv);
+        u[e] = (R)(sc[c] * user[(size_t)perm[c] * npv + j]);
+    }
 }
 
 template <typename R>
-__global__ void k_to_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm, const double *__restrict__ sc,
-                          const R *__restrict__ u, double *__restrict__ user)
+__global__ void __launch_bounds__(256) k_to_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm,
+                                                 const double *__restrict__ sc, const R *__restrict__ u, double *__restrict__ user)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nc) return;
-    const size_t uc = (size_t)perm[c];
-    const double s = 1.0 / sc[c];
-    for (int v = 0; v < nv; ++v)
-        for (int m = 0; m < np; ++m) user[(uc * nv + v) * np + m] = s * (double)u[sidx(nv, np, v, m, c)];
+    const int npv = nv * np;
+    const size_t n = (size_t)nc * npv;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / npv), j = (int)(e - (size_t)c * npv);
+        user[(size_t)perm[c] * npv + j] = (1.0 / sc[c]) * (double)u[e];
+    }
 }
 
 __global__ void k_flags_to_user(int nc, const int32_t *__restrict__ perm, const uint8_t *__restrict__ fl, uint8_t *__restrict__ out)
@@ -444,12 +447,16 @@ __global__ void k_flags_to_user(int nc, const int32_t *__restrict__ perm, const 
 template <typename R>
 void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st)
 {
-    k_from_user<R><<<(nc + 255) / 256, 256, 0, st>>>(nc, ld, nv, np, perm, sc, user, u);
+    const size_t n = (size_t)nc * nv * np;
+    const int grd = (int)std::min<size_t>((n + 255) / 256, 16384);
+    k_from_user<R><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, user, u);
 }
 template <typename R>
 void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, double *user, cudaStream_t st)
 {
-    k_to_user<R><<<(nc + 255) / 256, 256, 0, st>>>(nc, ld, nv, np, perm, sc, u, user);
+    const size_t n = (size_t)nc * nv * np;
+    const int grd = (int)std::min<size_t>((n + 255) / 256, 16384);
+    k_to_user<R><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, u, user);
 }
 template void launch_from_user<float>(int, int, int, int, const int32_t *, const double *, const double *, float *, cudaStream_t);
 template void launch_from_user<double>(int, int, int, int, const int32_t *, const double *, const double *, double *, cudaStream_t);
