@@ -114,11 +114,16 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
-def read_traffic(khash):
-    """DRAM bytes per launch of the stage kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_stage_euler_p2_dmr.md")
-    if not os.path.exists(p):
+# committed ncu summary of the stage kernel, per workload
+PROFILE_FILES = {"dmr": "k_stage_euler_p2_dmr.md", "ensemble": "k_stage_euler_p2_ensemble.md"}
+
+
+def read_traffic(khash, workload="dmr"):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary
+    of this workload, if there is one and it was taken on the current kernel
+    source (else None)."""
+    p = os.path.join(ROOT, "profiles", PROFILE_FILES.get(workload, ""))
+    if not os.path.isfile(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", txt)
@@ -241,7 +246,7 @@ def run_ours(args):
     achieved = nc * bpc / (stage_ms * 1e-3) / 1e9
     peak, peak_src = read_peak()
     khash = kernel_hash()
-    traffic = read_traffic(khash)
+    traffic = read_traffic(khash, args.workload)
 
     # end to end: pinned host state in, one step, state out, through the C interface
     host_in = torch.empty((nc, NV, NP), dtype=torch.float64, pin_memory=True).numpy()

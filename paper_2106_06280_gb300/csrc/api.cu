@@ -585,17 +585,21 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
 {
     if (!s || !s->mesh_ready || nsteps < 0) return fail(s, CSWDG_EINVAL, "step: no mesh or negative nsteps");
     const int use_cfl = !(dt > 0.0);
-    Ctl h;
-    if (cswdg_status r = read_ctl(s, &h)) return r;
-    h.t_next = h.t_next;  // the step starts from t_next (= current time)
-    h.dt_fixed = dt;
-    h.cfl = s->cfg.cfl;
-    h.t_end = t_end;
-    if (use_cfl && s->lam_stale)
-        if (cswdg_status r = refresh_lam(s, &h, nullptr)) return r;
-    if (cswdg_status r = write_ctl(s, &h)) return r;
+    // everything up to the final read of the control block is queued on the
+    // stream: the step parameters, the CFL maximum of a state set from outside
+    // (lam_bits cleared first), the step graphs; one host round trip per call
+    launch_set_step_params(s->ctl, dt, s->cfg.cfl, t_end, s->stream);
+    CK(cudaGetLastError());
+    if (use_cfl && s->lam_stale) {
+        CK(cudaMemsetAsync(&s->ctl->lam_bits, 0, sizeof(unsigned long long), s->stream));
+        if (s->fp32) launch_cfl<float>(s->eq, mesh_dev<float>(s), s->np, (const float *)s->U, s->ctl, s->stream);
+        else launch_cfl<double>(s->eq, mesh_dev<double>(s), s->np, (const double *)s->U, s->ctl, s->stream);
+        CK(cudaGetLastError());
+        s->lam_stale = false;
+    }
     if (cswdg_status r = get_graph(s, use_cfl)) return r;
     for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(s->graph[use_cfl], s->stream));
+    Ctl h;
     if (cswdg_status r = read_ctl(s, &h)) return r;
     h.t = h.t_next;
     if (t_out) *t_out = h.t_next;

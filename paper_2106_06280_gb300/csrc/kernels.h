@@ -38,6 +38,7 @@ void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, 
                   int lam_next, R *kx, Ctl *ctl, StageShape sh, cudaStream_t st);
 template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st);
 void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st);
+void launch_set_step_params(Ctl *ctl, double dt_fixed, double cfl, double t_end, cudaStream_t st);
 template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);
 template <typename R>
 void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st);

@@ -974,74 +974,83 @@ template void launch_detect<double>(int, int, const MeshDev<double> &, const dou
 // faces the ghost is integrated at the Gauss points as in detect_cell.  The
 // decision is the same product form, screened in the state precision, with
 // FP64 close calls.
+// KXRCF decision of cell c from its precursor record: the jump integral over
+// the inflow faces in face order (Sec. 3.1), compared in product form
 template <int EQ, int K, typename R>
+__device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R (&k8)[KX_STRIDE], R kap, const Ctl *ctl, double tfac, double ck,
+                                       R ck2, int c)
+{
+    constexpr int QF = Deg<K>::QF;
+    const Tab<R, K> &T = ltab<R, K>();
+    R num = R(0), lsum = R(0);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+        const R w = k8[KX_W0 + f];
+        if (w == R(0)) continue;  // outflow face
+        R J, nl;
+        if (w > R(0)) {
+            nl = w;
+            J = k8[KX_I0 + f] - k8[KX_O0 + f];
+        } else {
+            nl = -w;
+            const int code = M.nbr[f * M.ldc + c];
+            const BFace bf = M.bf[-code - 1];
+            const int kind = M.bc->kind[bf.tag];
+            if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
+                R go = R(0);
+                for (int g = 0; g < QF; ++g) go += T.fw[g] * ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), R(0));
+                J = k8[KX_I0 + f] - go;
+            } else {
+                J = R(0);  // transmissive and wall: the ghost indicator is the interior trace
+            }
+        }
+        num += nl * J;
+        lsum += nl;
+    }
+    const R nrm2 = k8[KX_NRM2];
+    if (!(lsum > R(0))) return 0;
+    const R denr = lsum * kap;
+    const R lhs = num * num, rhs = ck2 * denr * denr * nrm2;
+    if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) return lhs > rhs;
+    const double den = (double)lsum * (double)kap;
+    return (double)num * (double)num > ck * ck * den * den * (double)nrm2;
+}
+
+// Detection after a stage kernel: CPT cells per thread (cells c0, c0 + 128, ...
+// of the block's range, so every load instruction of a warp covers consecutive
+// records), all records and kappas loaded before the read of the step's active
+// flag; no load depends on another.  Flagged cells are compacted per warp.
+template <int EQ, int K, typename R, int CPT>
 __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__restrict__ kx, Ctl *ctl, double tfac, double ck, R ck2,
                                                    int all, uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
 {
-    constexpr int QF = Deg<K>::QF;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int flag = 0;
-    // the cell's record (own face means, inflow weights and norm, the
-    // neighbours' face means) and kappa are loaded before the read of the step's
-    // active flag; no load depends on another
-    R k8[KX_STRIDE] = {}, kap = R(0);
-    const int ld = M.ldc;
-    if (c < M.nc) {
-        load_kx<R>(kx, c, k8);
-        if (!all) kap = M.geo[G_KAPPA * ld + c];
+    const int c0 = blockIdx.x * blockDim.x * CPT + threadIdx.x;
+    R k8[CPT][KX_STRIDE] = {}, kap[CPT] = {};
+#pragma unroll
+    for (int i = 0; i < CPT; ++i) {
+        const int c = c0 + i * (int)blockDim.x;
+        if (c < M.nc) {
+            load_kx<R>(kx, c, k8[i]);
+            if (!all) kap[i] = M.geo[G_KAPPA * M.ldc + c];
+        }
     }
     if (!ctl->active) return;
-    if (c < M.nc) {
-        if (all) {
-            flag = 1;
-        } else {
-            const Tab<R, K> &T = ltab<R, K>();
-            R num = R(0), lsum = R(0);
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const R w = k8[KX_W0 + f];
-                if (w == R(0)) continue;  // outflow face
-                R J, nl;
-                if (w > R(0)) {
-                    nl = w;
-                    J = k8[KX_I0 + f] - k8[KX_O0 + f];
-                } else {
-                    nl = -w;
-                    const int code = M.nbr[f * ld + c];
-                    const BFace bf = M.bf[-code - 1];
-                    const int kind = M.bc->kind[bf.tag];
-                    if (kind == BC_DIRICHLET || kind == BC_SHOCKLINE) {
-                        R go = R(0);
-                        for (int g = 0; g < QF; ++g) go += T.fw[g] * ghost0<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), R(0));
-                        J = k8[KX_I0 + f] - go;
-                    } else {
-                        J = R(0);  // transmissive and wall: the ghost indicator is the interior trace
-                    }
-                }
-                num += nl * J;
-                lsum += nl;
-            }
-            const R nrm2 = k8[KX_NRM2];
-            if (lsum > R(0)) {
-                const R denr = lsum * kap;
-                const R lhs = num * num, rhs = ck2 * denr * denr * nrm2;
-                if (rabs(lhs - rhs) > R(1e-3) * (lhs + rhs)) {
-                    flag = lhs > rhs;
-                } else {
-                    const double den = (double)lsum * (double)kap;
-                    flag = (double)num * (double)num > ck * ck * den * den * (double)nrm2;
-                }
-            }
+    for (int i = 0; i < CPT; ++i) {
+        const int c = c0 + i * (int)blockDim.x;
+        int flag = 0;
+        if (c < M.nc) {
+            flag = all ? 1 : kx_flag<EQ, K, R>(M, k8[i], kap[i], ctl, tfac, ck, ck2, c);
+            flags[c] = (uint8_t)flag;
         }
-        flags[c] = (uint8_t)flag;
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, flag);
-    if (mask) {
-        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
+        const unsigned mask = __ballot_sync(0xffffffffu, flag);
+        if (mask) {
+            const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(&ctl->nflag, __popc(mask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (flag) flist[base + __popc(mask & ((1u << lane) - 1u))] = c;
+        }
     }
 }
 
@@ -1049,9 +1058,10 @@ template <typename R>
 void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *kx, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
                       int32_t *flist, cudaStream_t st)
 {
-    const int blk = 128, grd = (M.nc + blk - 1) / blk;
+    constexpr int CPT = 1;  // 2 and 4 cells per thread measured slower (fewer warps in flight)
+    const int blk = 128, grd = (M.nc + blk * CPT - 1) / (blk * CPT);
     const R ck2 = (R)(ck * ck);
-#define CSW_DK(E, KK) k_detect_kx<E, KK, R><<<grd, blk, 0, st>>>(M, kx, ctl, tfac, ck, ck2, all, flags, flist)
+#define CSW_DK(E, KK) k_detect_kx<E, KK, R, CPT><<<grd, blk, 0, st>>>(M, kx, ctl, tfac, ck, ck2, all, flags, flist)
     if (eq == BURGERS && k == 1) CSW_DK(BURGERS, 1);
     else if (eq == BURGERS && k == 2) CSW_DK(BURGERS, 2);
     else if (eq == EULER && k == 1) CSW_DK(EULER, 1);

@@ -377,6 +377,18 @@ template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const
 template void launch_cfl<float>(int, const MeshDev<float> &, int, const float *, Ctl *, cudaStream_t);
 template void launch_cfl<double>(int, const MeshDev<double> &, int, const double *, Ctl *, cudaStream_t);
 
+// the step parameters of a cswdg_step call, set on the stream (no host round trip)
+__global__ void k_set_step_params(Ctl *ctl, double dt_fixed, double cfl, double t_end)
+{
+    ctl->dt_fixed = dt_fixed;
+    ctl->cfl = cfl;
+    ctl->t_end = t_end;
+}
+void launch_set_step_params(Ctl *ctl, double dt_fixed, double cfl, double t_end, cudaStream_t st)
+{
+    k_set_step_params<<<1, 1, 0, st>>>(ctl, dt_fixed, cfl, t_end);
+}
+
 void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st) { k_begin_step<<<1, 1, 0, st>>>(ctl, use_cfl); }
 
 // ---------------------------------------------------------------------------
