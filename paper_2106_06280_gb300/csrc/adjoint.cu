@@ -56,7 +56,7 @@ template <int EQ, typename R> __device__ __forceinline__ void flux_jac_T(const R
         out[0] = U[0] * (a[0] + b[0]);
         return;
     }
-    const R ir = rrcp(U[0]);
+    const R ir = frcp(U[0]);
     const R u = U[1] * ir, v = U[2] * ir, gt = gam - R(1);
     const R q2 = u * u + v * v;
     const R p = gt * (U[3] - R(0.5) * U[0] * q2);
@@ -70,11 +70,11 @@ template <int EQ, typename R> __device__ __forceinline__ void flux_jac_T(const R
 // gradient of the wave speed s = |u.n| + c of the local Lax-Friedrichs flux
 template <typename R> __device__ __forceinline__ void speed_grad(const R *U, R gam, R nx, R ny, R *ds)
 {
-    const R ir = rrcp(U[0]);
+    const R ir = frcp(U[0]);
     const R u = U[1] * ir, v = U[2] * ir, gt = gam - R(1);
     const R q2 = u * u + v * v;
     const R p = gt * (U[3] - R(0.5) * U[0] * q2);
-    const R c = rsqrt_fast(gam * p * ir);
+    const R c = fsqrt(gam * p * ir);
     const R un = u * nx + v * ny, sg = (un > R(0)) ? R(1) : ((un < R(0)) ? R(-1) : R(0));
     const R k = gam / (R(2) * c * U[0]);
     ds[0] = sg * (-un * ir) + k * (R(0.5) * gt * q2 - p * ir);
@@ -101,11 +101,11 @@ __device__ __forceinline__ void llf_adj(const R *UL, const R *UR, R nx, R ny, R 
         return;
     }
     // speeds as the forward flux evaluates them
-    const R irl = rrcp(UL[0]), irr = rrcp(UR[0]);
+    const R irl = frcp(UL[0]), irr = frcp(UR[0]);
     const R unl = (UL[1] * nx + UL[2] * ny) * irl, unr = (UR[1] * nx + UR[2] * ny) * irr;
     const R pl = (gam - R(1)) * (UL[3] - R(0.5) * (UL[1] * UL[1] + UL[2] * UL[2]) * irl);
     const R pr = (gam - R(1)) * (UR[3] - R(0.5) * (UR[1] * UR[1] + UR[2] * UR[2]) * irr);
-    const R cl = rsqrt_fast(gam * pl * irl), cr = rsqrt_fast(gam * pr * irr);
+    const R cl = fsqrt(gam * pl * irl), cr = fsqrt(gam * pr * irr);
     const R sl = rabs(unl) + cl, sr = rabs(unr) + cr;
     const bool left = sl > sr;
     const R a = left ? sl : sr;
@@ -142,17 +142,22 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
 
     // volume: d/du of sum_q w_q [ (dr psi)(g0 f + g1 g) + (ds psi)(g2 f + g3 g) ] . lambda
     for (int q = 0; q < QV; ++q) {
-        R U[NV], a[NV], b[NV], t[NV];
+        R U[NV], a[NV], b[NV], t[NV], dx[NP], dy[NP];
+        // physical derivatives of the basis at the point, weight folded in
+        for (int m = 0; m < NP; ++m) {
+            dx[m] = T.vdrw[q][m] * g0 + T.vdsw[q][m] * g2;
+            dy[m] = T.vdrw[q][m] * g1 + T.vdsw[q][m] * g3;
+        }
         for (int v = 0; v < NV; ++v) {
             R su = R(0), sa = R(0), sb = R(0);
             for (int m = 0; m < NP; ++m) {
                 su += uc[v][m] * T.vphi[q][m];
-                sa += lc[v][m] * (T.vdr[q][m] * g0 + T.vds[q][m] * g2);
-                sb += lc[v][m] * (T.vdr[q][m] * g1 + T.vds[q][m] * g3);
+                sa += lc[v][m] * dx[m];
+                sb += lc[v][m] * dy[m];
             }
             U[v] = su;
-            a[v] = T.vw[q] * sa;
-            b[v] = T.vw[q] * sb;
+            a[v] = sa;
+            b[v] = sb;
         }
         flux_jac_T<EQ, R>(U, gam, a, b, t);
         for (int v = 0; v < NV; ++v)
@@ -162,6 +167,7 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
     // faces: the canonical flux enters this cell's residual with -|n~| w_g psi and
     // the neighbour's with the neighbour's factors at the reversed point
     const unsigned nbf = M.nbf[c];
+#pragma unroll 1
     for (int f = 0; f < 3; ++f) {
         const R nx = M.geo[(G_N0X + 3 * f) * ld + c], ny = M.geo[(G_N0Y + 3 * f) * ld + c], nl = M.geo[(G_N0L + 3 * f) * ld + c];
         const int code = M.nbr[f * ld + c];
@@ -181,6 +187,7 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
             bf = M.bf[-code - 1];
             kind = M.bc->kind[bf.tag];
         }
+#pragma unroll 1
         for (int g_ = 0; g_ < QF; ++g_) {
             const int gr = QF - 1 - g_;
             R Ui[NV], Uo[NV], mu[NV];

@@ -956,6 +956,17 @@ cswdg_status cswdg_limit_adjoint(cswdg_solver *s, double t, const double *modes_
 //   g0 = 1/3 b3 + 3/4 b2;  w = 1/4 b2;  h1 = w + dt L'(u1)^T w;  b1 = Lam_1'^T h1
 //   g0 += b1 + dt L'(u0)^T b1
 // ---------------------------------------------------------------------------
+// the time and step of one recomputed or reversed step of the adjoint sweep,
+// set on the stream (no host round trip)
+static __global__ void k_set_clock(Ctl *ctl, double t, double dt)
+{
+    ctl->t = t;
+    ctl->dt = dt;
+    ctl->dtf = (float)dt;
+    ctl->active = 1;
+}
+static void launch_set_clock(Ctl *ctl, double t, double dt, cudaStream_t st) { k_set_clock<<<1, 1, 0, st>>>(ctl, t, dt); }
+
 cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int32_t checkpoint_every, const double *u0_user,
                                  const double *gT_user, double *uT_user, double *g0_user, double *dt_host)
 {
@@ -1052,11 +1063,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             char *base = seg + (size_t)NS * (n - n0) * bytes;
             int32_t *fl = lim ? fls + (size_t)3 * (n - n0) * s->ldc : nullptr;
             int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
-            Ctl ws = hf;
-            ws.t = times[n];
-            ws.dt = dtv[n];
-            ws.active = 1;
-            STR(write_ctl(s, &ws));
+            launch_set_clock(s->ctl, times[n], dtv[n], s->stream);
             CKR(cudaMemcpyAsync(base, s->U, bytes, cudaMemcpyDeviceToDevice, s->stream));
             void *outs[3] = {s->A, s->B, s->U};
             const void *ins[3] = {s->U, s->A, s->B};
@@ -1077,11 +1084,7 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             const char *base = seg + (size_t)NS * (n - n0) * bytes;
             const int32_t *fl = lim ? fls + (size_t)3 * (n - n0) * s->ldc : nullptr;
             const int32_t *nf = lim ? nfs + 3 * (n - n0) : nullptr;
-            Ctl ws = hf;
-            ws.t = times[n];
-            ws.dt = dtv[n];
-            ws.active = 1;
-            STR(write_ctl(s, &ws));
+            launch_set_clock(s->ctl, times[n], dtv[n], s->stream);
             const void *u0s = base, *v1 = base + bytes, *v2 = base + 2 * bytes, *v3 = base + 3 * bytes, *u1s = base + 4 * bytes,
                        *u2s = base + 5 * bytes;
             auto run = [&](auto tag) {
