@@ -124,8 +124,9 @@ __device__ __forceinline__ void llf_adj(const R *UL, const R *UR, R nx, R ny, R 
 }
 
 template <int EQ, int K, typename R>
-__global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ lam, R *__restrict__ grad,
-                                                 double tfac, const Ctl *__restrict__ ctl)
+__global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ lam, R *grad,
+                                                 double tfac, const Ctl *__restrict__ ctl, const R *x, R ax, const R *y, R ay,
+                                                 R beta)
 {
     constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,23 +243,46 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
                 for (int m = 0; m < NP; ++m) g[v][m] += T.fphi[f][g_][m] * dUi[v];
         }
     }
+    // epilogue: grad = ax x + ay y + beta g (x, y nullable; grad may alias x or
+    // y, never u or lam: a cell reads and writes only its own entries of them)
+    if (x || y) {
+        R xv[NV][NP];
+        if (x) {
+            load_cell<NV, NP>(x, c, xv);
+            for (int v = 0; v < NV; ++v)
+                for (int m = 0; m < NP; ++m) g[v][m] = ax * xv[v][m] + beta * g[v][m];
+        } else {
+            for (int v = 0; v < NV; ++v)
+                for (int m = 0; m < NP; ++m) g[v][m] = beta * g[v][m];
+        }
+        if (y) {
+            load_cell<NV, NP>(y, c, xv);
+            for (int v = 0; v < NV; ++v)
+                for (int m = 0; m < NP; ++m) g[v][m] += ay * xv[v][m];
+        }
+    } else if (beta != R(1)) {
+        for (int v = 0; v < NV; ++v)
+            for (int m = 0; m < NP; ++m) g[v][m] = beta * g[v][m];
+    }
     store_cell<NV, NP>(grad, c, g);
 }
 
 template <typename R>
 void launch_rhs_adjoint(int eq, int k, const MeshDev<R> &M, const R *u, const R *lam, R *grad, double tfac, const Ctl *ctl,
-                        cudaStream_t st)
+                        cudaStream_t st, const R *x, R ax, const R *y, R ay, R beta)
 {
     const int blk = 128, grd = (M.nc + blk - 1) / blk;
-    if (eq == BURGERS && k == 1) k_rhs_adj<BURGERS, 1, R><<<grd, blk, 0, st>>>(M, u, lam, grad, tfac, ctl);
-    else if (eq == BURGERS && k == 2) k_rhs_adj<BURGERS, 2, R><<<grd, blk, 0, st>>>(M, u, lam, grad, tfac, ctl);
-    else if (eq == EULER && k == 1) k_rhs_adj<EULER, 1, R><<<grd, blk, 0, st>>>(M, u, lam, grad, tfac, ctl);
-    else k_rhs_adj<EULER, 2, R><<<grd, blk, 0, st>>>(M, u, lam, grad, tfac, ctl);
+#define CSW_RA(E, KK) k_rhs_adj<E, KK, R><<<grd, blk, 0, st>>>(M, u, lam, grad, tfac, ctl, x, ax, y, ay, beta)
+    if (eq == BURGERS && k == 1) CSW_RA(BURGERS, 1);
+    else if (eq == BURGERS && k == 2) CSW_RA(BURGERS, 2);
+    else if (eq == EULER && k == 1) CSW_RA(EULER, 1);
+    else CSW_RA(EULER, 2);
+#undef CSW_RA
 }
 template void launch_rhs_adjoint<float>(int, int, const MeshDev<float> &, const float *, const float *, float *, double, const Ctl *,
-                                        cudaStream_t);
+                                        cudaStream_t, const float *, float, const float *, float, float);
 template void launch_rhs_adjoint<double>(int, int, const MeshDev<double> &, const double *, const double *, double *, double,
-                                         const Ctl *, cudaStream_t);
+                                         const Ctl *, cudaStream_t, const double *, double, const double *, double, double);
 
 // out = a x + b y (y nullable), elementwise over n entries (state arrays in
 // the internal layout); out may alias x or y

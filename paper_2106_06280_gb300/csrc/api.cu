@@ -1053,8 +1053,9 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
     }
     if (dt_host) std::copy(dtv.begin(), dtv.end(), dt_host);
     if (uT_user) STR(download_modes(s, s->U, uT_user));
-    // reverse sweep
-    STR(upload_modes(s, gT_user, ga, true));
+    // reverse sweep; the four adjoint buffers change roles by pointer swaps
+    char *pa = ga, *pt = gt, *pw = gw, *px = gx;
+    STR(upload_modes(s, gT_user, pa, true));
     for (int64_t sg = nck - 1; sg >= 0; --sg) {
         const int64_t n0 = sg * ce, n1 = std::min(nsteps, n0 + ce);
         CKR(cudaMemcpyAsync(s->U, ck + (size_t)sg * bytes, bytes, cudaMemcpyDeviceToDevice, s->stream));
@@ -1087,40 +1088,42 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
             launch_set_clock(s->ctl, times[n], dtv[n], s->stream);
             const void *u0s = base, *v1 = base + bytes, *v2 = base + 2 * bytes, *v3 = base + 3 * bytes, *u1s = base + 4 * bytes,
                        *u2s = base + 5 * bytes;
+            // the transposed stage updates with the linear combinations fused into
+            // the operator adjoint's epilogue (it is linear in its adjoint input):
+            //   h2 = 2/3 (b3 + dt L'(u2)^T b3);  a = 1/3 b3 + 3/4 b2;
+            //   h1 = 1/4 (b2 + dt L'(u1)^T b2);  g0 = a + b1 + dt L'(u0)^T b1
+            // limiter adjoints write a spare buffer, whose pointer then swaps in
             auto run = [&](auto tag) {
                 using R = decltype(tag);
                 const MeshDev<R> M = mesh_dev<R>(s);
                 const R d = (R)dtv[n];
-                R *a = (R *)ga, *wv = (R *)gw, *tv = (R *)gt, *xv = (R *)gx;
+                R *a = (R *)pa, *t = (R *)pt, *w = (R *)pw, *x = (R *)px;
                 if (lim) {  // b3 = Lam_3'^T g
-                    limit_adjoint_dev<R>(s, v3, fl + 2 * (size_t)s->ldc, nf + 2, 1.0, a, xv, nstate, s->stream);
-                    cudaMemcpyAsync(a, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                    limit_adjoint_dev<R>(s, v3, fl + 2 * (size_t)s->ldc, nf + 2, 1.0, a, x, nstate, s->stream);
+                    std::swap(a, x);
                 }
-                launch_axpby<R>(nstate, R(2) / R(3), a, R(0), nullptr, wv, grid, s->stream);
-                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u2s, wv, tv, 0.5, s->ctl, s->stream);
-                launch_axpby<R>(nstate, R(1), wv, d, tv, tv, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u2s, a, t, 0.5, s->ctl, s->stream, a, R(2) / R(3), nullptr, R(0),
+                                      R(2) / R(3) * d);
                 if (lim) {  // b2 = Lam_2'^T h2
-                    limit_adjoint_dev<R>(s, v2, fl + (size_t)s->ldc, nf + 1, 0.5, tv, xv, nstate, s->stream);
-                    cudaMemcpyAsync(tv, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                    limit_adjoint_dev<R>(s, v2, fl + (size_t)s->ldc, nf + 1, 0.5, t, x, nstate, s->stream);
+                    std::swap(t, x);
                 }
-                launch_axpby<R>(nstate, R(1) / R(3), a, R(0.75), tv, a, grid, s->stream);
-                launch_axpby<R>(nstate, R(0.25), tv, R(0), nullptr, wv, grid, s->stream);
-                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u1s, wv, tv, 1.0, s->ctl, s->stream);
-                launch_axpby<R>(nstate, R(1), wv, d, tv, tv, grid, s->stream);
+                launch_axpby<R>(nstate, R(1) / R(3), a, R(0.75), t, a, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u1s, t, w, 1.0, s->ctl, s->stream, t, R(0.25), nullptr, R(0),
+                                      R(0.25) * d);
                 if (lim) {  // b1 = Lam_1'^T h1
-                    limit_adjoint_dev<R>(s, v1, fl, nf, 1.0, tv, xv, nstate, s->stream);
-                    cudaMemcpyAsync(tv, xv, bytes, cudaMemcpyDeviceToDevice, s->stream);
+                    limit_adjoint_dev<R>(s, v1, fl, nf, 1.0, w, x, nstate, s->stream);
+                    std::swap(w, x);
                 }
-                launch_axpby<R>(nstate, R(1), a, R(1), tv, a, grid, s->stream);
-                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u0s, tv, wv, 0.0, s->ctl, s->stream);
-                launch_axpby<R>(nstate, R(1), a, d, wv, a, grid, s->stream);
+                launch_rhs_adjoint<R>(s->eq, s->k, M, (const R *)u0s, w, a, 0.0, s->ctl, s->stream, a, R(1), w, R(1), d);
+                pa = (char *)a; pt = (char *)t; pw = (char *)w; px = (char *)x;
             };
             if (s->fp32) run(float(0));
             else run(double(0));
             CKR(cudaGetLastError());
         }
     }
-    STR(download_modes(s, ga, g0_user, true));
+    STR(download_modes(s, pa, g0_user, true));
     // leave the solver at u^N and t^N
     CKR(cudaMemcpyAsync(s->U, uN, bytes, cudaMemcpyDeviceToDevice, s->stream));
     Ctl fin = hf;

@@ -48,10 +48,12 @@ void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_
 template <typename R>
 void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st);
 
-// adjoint of the operator: grad = (d L_h / d u)^T lam at the stage time t + tfac dt
+// adjoint of the operator at the stage time t + tfac dt, combined on output:
+// grad = ax x + ay y + beta (d L_h / d u)^T lam (x, y nullable; grad may alias
+// x or y but not u or lam)
 template <typename R>
 void launch_rhs_adjoint(int eq, int k, const MeshDev<R> &M, const R *u, const R *lam, R *grad, double tfac, const Ctl *ctl,
-                        cudaStream_t st);
+                        cudaStream_t st, const R *x = nullptr, R ax = R(0), const R *y = nullptr, R ay = R(0), R beta = R(1));
 
 // adjoint of a limiter pass with frozen flags (flist, *nflag_dev): gout = gin
 // with the flagged cells' modes 1..np-1 replaced by the reconstruction's
