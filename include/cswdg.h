@@ -208,6 +208,17 @@ cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_ho
  * Errors: EINVAL. */
 cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid);
 
+/* Self-test of the device error path (no counterpart in the paper): launches
+ * one warp that waits, with the wait primitive of the reconstruction kernel's
+ * bounded waits and at most `polls` polls (1 .. 4,194,304, the kernel's own
+ * limit), on a shared-memory barrier phase that never completes, so the wait
+ * runs out and sets the timeout error bit; no copy or other work is pending
+ * on the barrier, nothing faults or hangs.  Returns CSWDG_ETIMEOUT (the status
+ * any bounded wait that ran out produces) and clears the bit, so the solver
+ * stays usable; the state is not touched.
+ * Errors: EINVAL (no mesh, polls out of range), ECUDA. */
+cswdg_status cswdg_selftest_timeout(cswdg_solver *s, int32_t polls);
+
 /* Kernels one cswdg_step step launches (use_cfl: dt <= 0). */
 int32_t cswdg_launches_per_step(const cswdg_solver *s, int32_t use_cfl);
 

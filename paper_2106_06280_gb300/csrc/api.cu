@@ -277,7 +277,7 @@ cswdg_status check_err(cswdg_solver *s, Ctl *h)
         Ctl c = *h;
         c.err = 0;
         write_ctl(s, &c);
-        return fail(s, CSWDG_ETIMEOUT, "bounded device wait expired (operator-block copy)");
+        return fail(s, CSWDG_ETIMEOUT, "bounded device wait expired");
     }
     return CSWDG_OK;
 }
@@ -604,6 +604,16 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
     h.t = h.t_next;
     if (t_out) *t_out = h.t_next;
     return check_err(s, &h);
+}
+
+cswdg_status cswdg_selftest_timeout(cswdg_solver *s, int32_t polls)
+{
+    if (!s || !s->mesh_ready || polls < 1 || polls > (1 << 22)) return fail(s, CSWDG_EINVAL, "selftest_timeout: no mesh or bad poll count");
+    launch_selftest_timeout(s->ctl, polls, s->stream);
+    CK(cudaGetLastError());
+    Ctl h;
+    if (cswdg_status r = read_ctl(s, &h)) return r;
+    return check_err(s, &h);  // reports ETIMEOUT and clears the bit
 }
 
 cswdg_status cswdg_profile_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *ms_host, int64_t *launches_host)

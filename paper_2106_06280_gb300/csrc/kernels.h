@@ -39,6 +39,9 @@ void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, 
 template <typename R> void launch_cfl(int eq, const MeshDev<R> &M, int np, const R *u, Ctl *ctl, cudaStream_t st);
 void launch_begin_step(Ctl *ctl, int use_cfl, cudaStream_t st);
 void launch_set_step_params(Ctl *ctl, double dt_fixed, double cfl, double t_end, cudaStream_t st);
+// one warp waits (at most polls polls) on an mbarrier phase that never
+// completes; sets ERR_TIMEOUT
+void launch_selftest_timeout(Ctl *ctl, int polls, cudaStream_t st);
 template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);
 template <typename R>
 void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st);

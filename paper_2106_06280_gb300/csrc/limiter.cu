@@ -1108,6 +1108,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
                  : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// poll limit of every bounded mbarrier wait (well under a second on this GPU)
+constexpr int MBAR_POLLS = 1 << 22;
 // wait for the phase with the given parity, at most `limit` polls (each poll
 // may itself suspend for a hardware-defined time); true when it completed
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, int limit)
@@ -1116,6 +1122,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+
+// Self-test of the bounded-wait error path (no counterpart in the paper): one
+// warp waits, with the reconstruction kernel's wait primitive and a short poll
+// limit, on an mbarrier phase that needs two arrivals and receives one (no
+// copy is pending on it).  The wait runs out, ERR_TIMEOUT is set for the host
+// and the warp returns.
+__global__ void k_selftest_timeout(Ctl *ctl, int polls)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        mbar_arrive(&bar);
+    }
+    __syncwarp();
+    const bool done = mbar_wait_bounded(&bar, 0, polls);
+    if (!__all_sync(0xffffffffu, done) && threadIdx.x == 0) atomicOr(&ctl->err, ERR_TIMEOUT);
+}
+void launch_selftest_timeout(Ctl *ctl, int polls, cudaStream_t st) { k_selftest_timeout<<<1, 32, 0, st>>>(ctl, polls); }
 
 // CSWENO reconstruction of the flagged cells flist[0 .. nflag) into
 // lim_out[idx], from the unlimited state u.  Euler: eight lanes per cell (four
@@ -1196,7 +1220,7 @@ __global__ void __launch_bounds__(128) k_limit_euler_staged(MeshDev<R> M, const 
                                                             R *__restrict__ lim_out)
 {
     constexpr int NP = Deg<K>::NP, NV = 4, SZ = Ops<K>::SIZE, G = 8, CPW = 32 / G;
-    constexpr int POLLS = 1 << 22;
+    constexpr int POLLS = MBAR_POLLS;
     extern __shared__ __align__(16) unsigned char dsm[];
     if (!ctl->active) return;
     const int n = ctl->nflag;

@@ -65,6 +65,7 @@ def _load():
         "cswdg_internal_layout": ([vp, C.POINTER(i64), C.POINTER(i32)], C.c_int),
         "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
         "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
+        "cswdg_selftest_timeout": ([vp, i32], C.c_int),
         "cswdg_autotune": ([vp, dp, C.POINTER(i32)], C.c_int),
         "cswdg_rhs_adjoint": ([vp, C.c_double, dp, dp, dp], C.c_int),
         "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp, dp], C.c_int),
@@ -84,7 +85,7 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_launches_per_step", "cswdg_get_time",
             "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
-            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_autotune", "cswdg_rhs_adjoint",
+            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_selftest_timeout", "cswdg_autotune", "cswdg_rhs_adjoint",
             "cswdg_adjoint_steps", "cswdg_limit_adjoint",
             "cswdg_set_stage_shape"]
 TUNE_CANDIDATES = 7
@@ -244,6 +245,10 @@ class Solver:
         dts = np.zeros(int(nsteps))
         self._chk(lib.cswdg_adjoint_steps(self.h, dt, nsteps, checkpoint_every, _p(u0), _p(gT), _p(uT), _p(g0), _p(dts)))
         return (uT, g0, dts) if return_dts else (uT, g0)
+
+    def selftest_timeout(self, polls=4096):
+        """Run the bounded-wait self-test; raises CswdgError (ETIMEOUT) as designed."""
+        self._chk(lib.cswdg_selftest_timeout(self.h, polls))
 
     def limit_adjoint(self, modes, lam, t=0.0):
         """(dLim/du)^T lam at the state modes with the flags frozen; returns (grad, flags)."""

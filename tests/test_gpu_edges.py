@@ -70,3 +70,30 @@ def test_argument_errors_are_statuses(csw, cuda_stream):
     with pytest.raises(csw.CswdgError, match="EINVAL"):
         s.limit_adjoint(u, u, 0.0)
     s.close()
+
+
+def test_bounded_wait_timeout_is_a_status(csw, cuda_stream):
+    """A device wait that runs out ends its kernel with an error bit that the host
+    reports as ETIMEOUT (the self-test waits on a barrier phase that nothing
+    completes, with a short poll limit); the solver stays usable: a step
+    afterwards matches the oracle."""
+    import time
+
+    pb = W.burgers_sine(4, seed=11)
+    s = csw.Solver(0, 2, csw.FP64, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    t0 = time.perf_counter()
+    with pytest.raises(csw.CswdgError, match="ETIMEOUT"):
+        s.selftest_timeout(4096)
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(csw.CswdgError, match="EINVAL"):
+        s.selftest_timeout(0)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    u = o.project(pb.u0)
+    s.write_modes(u)
+    s.set_time(0.0)
+    dt = 0.5 * o.cfl_dt(u, 0.1)
+    s.step(dt, 1, 1e9)
+    uo, _, st = o.step(u, 0.0, dt)
+    assert st == 0 and rel(s.read_modes(), uo) < 1e-11
+    s.close()
