@@ -18,12 +18,14 @@ workload (a fixed random subset of cells of the full mesh) instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -134,23 +136,27 @@ def read_traffic(khash, workload="dmr"):
 
 
 class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples (every 50 ms) around the
+    timed region; stop() keeps the samples whose timestamps fall inside the
+    host-side window of the timed region (all samples when none do, which the
+    result says)."""
+
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"cswdg_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self, dev):
+    def stop(self, dev, t0=None, t1=None):
         if self.proc is None:
             return None
         time.sleep(0.15)
@@ -160,24 +166,31 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9 or f[0] != str(dev):
+            if len(f) < 10 or f[1] != str(dev):
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        inside = [r for r in rows if r[0] is not None and t0 is not None and t0 <= r[0] <= t1]
+        use = inside if inside else rows
+        if not use:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": float(max(r[2] for r in use)),
+                "reasons": sorted({n for r in use for n in r[3]}), "samples": len(use),
+                "window": "timed region" if inside else "around the timed region"}
 
 
 def setup_solver(csw, precision, stream, seed=3, workload="dmr", shape=None):
@@ -224,8 +237,10 @@ def run_ours(args):
     clocks = ClockSampler()
     if rk == 0:
         clocks.start()
+        time.sleep(0.1)  # the sampler is running before the timed region starts
     barrier()
     torch.cuda.synchronize()
+    w0 = time.time()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     s.step(0.0, args.steps, t_end)
@@ -233,7 +248,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop(lr) if rk == 0 else None
+    w1 = time.time()
+    clk = clocks.stop(lr, w0, w1) if rk == 0 else None
     if ws > 1:
         ms = max_over_ranks(ms, "cuda")
     value = whole_job_rate(float(nc) * NP * NV * 3 * args.steps, ws, ms)
@@ -375,11 +391,10 @@ def run_ours(args):
     return out
 
 
-def cpu_baseline(sample, seed=3, workload="dmr"):
-    """The FP64 oracle as it stands, single thread, on a fixed random sample of
-    the cells of the same mesh and initial state: one SSP-RK3 step's work on
-    the sample = 3 x (operator on the sample + KXRCF on the sample +
-    reconstruction of the flagged sample cells)."""
+def cpu_prepare(sample, seed=3, workload="dmr"):
+    """The FP64 oracle on a fixed random sample of the cells of the same mesh
+    and initial state: the sample, its two-cell neighbourhood projected and
+    its neighbours reconstructed once (as the GPU run's initial condition)."""
     import oracle
     pb = make_problem(workload, seed)
     o = oracle.Oracle(pb, k=K, limiter=1)
@@ -395,6 +410,14 @@ def cpu_baseline(sample, seed=3, workload="dmr"):
     o.project_cells(pb.u0, near2, u)
     lim, _ = oa.limit_cells(u, near)
     u[near] = lim
+    return {"o": o, "u": u, "cells": cells, "nc": pb.mesh.nc}
+
+
+def cpu_time(prep, n):
+    """One SSP-RK3 step's work of the oracle, single thread, on the first n
+    sample cells: 3 x (operator + KXRCF on them + reconstruction of the flagged
+    ones).  Returns (seconds, flagged cells per stage)."""
+    o, u, cells = prep["o"], prep["u"], prep["cells"][:n]
     t0 = time.perf_counter()
     nflag = 0
     for _ in range(3):
@@ -404,10 +427,19 @@ def cpu_baseline(sample, seed=3, workload="dmr"):
         nflag += len(flagged)
         if len(flagged):
             o.limit_cells(u, flagged)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0, nflag // 3
+
+
+def cpu_baseline(sample, seed=3, workload="dmr"):
+    """The FP64 oracle as it stands, single thread, on a fixed random sample of
+    the cells of the same mesh and initial state: one SSP-RK3 step's work on
+    the sample = 3 x (operator on the sample + KXRCF on the sample +
+    reconstruction of the flagged sample cells)."""
+    prep = cpu_prepare(sample, seed, workload)
+    dt, nflag = cpu_time(prep, sample)
     return {"value": sample * NP * NV * 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} random cells of the {pb.mesh.nc:,}-cell mesh at the initial state, one SSP-RK3 step's work "
-                      f"(3 x operator + KXRCF on the sample, CSWENO on its flagged cells: {nflag // 3} per stage); "
+            "sample": f"{sample} random cells of the {prep['nc']:,}-cell mesh at the initial state, one SSP-RK3 step's work "
+                      f"(3 x operator + KXRCF on the sample, CSWENO on its flagged cells: {nflag} per stage); "
                       f"{dt:.1f} s",
             "seconds": dt}
 
@@ -416,18 +448,27 @@ def run_reference(args):
     ws, rk, lr = dist_info()
     if rk != 0:
         return None
-    vals = []
+    # each step times one SSP-RK3 step's work on a sample of the cells; the
+    # sample shrinks with the step count so that the whole run stays bounded
+    # (about 20 steps' worth of --ref-sample cells, at least 100 cells a step)
+    nsteps = max(1, args.steps)
+    n = max(100, min(args.ref_sample, (20 * args.ref_sample) // nsteps))
+    prep = cpu_prepare(args.ref_sample, workload=args.workload)
     for _ in range(args.warmup):
-        pass
+        cpu_time(prep, min(n, 100))
+    vals = []
     t0 = time.perf_counter()
-    cb = None
-    for _ in range(max(1, args.steps)):
-        cb = cpu_baseline(args.ref_sample, workload=args.workload)
-        vals.append(cb["value"])
+    nflag = 0
+    for _ in range(nsteps):
+        dt, nflag = cpu_time(prep, n)
+        vals.append(n * NP * NV * 3 / dt)
     t1 = time.perf_counter()
+    cb = {"sample": f"{n} random cells of the {prep['nc']:,}-cell mesh per step (one SSP-RK3 step's work: 3 x operator + "
+                    f"KXRCF on the sample, CSWENO on its flagged cells, {nflag} in the last stage), median over "
+                    f"{nsteps} steps"}
     value = float(np.median(vals))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * (t1 - t0) / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * (t1 - t0) / nsteps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOADS[args.workload], "degree": K},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
@@ -437,14 +478,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dmr", choices=sorted(WORKLOADS))
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--fp32-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--fp32-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps", type=int, default=100)
     ap.add_argument("--l1-steps", type=int, default=20)
     ap.add_argument("--stage-shape", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
