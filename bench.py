@@ -166,31 +166,41 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        rows = []
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 10 or f[1] != str(dev):
-                continue
-            try:
-                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-            except ValueError:
-                ts = None
-            try:
-                rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10]) if v.lower() == "active"]))
-            except ValueError:
-                continue
+        out = parse_clock_samples(self.path, dev, t0, t1)
         try:
             os.remove(self.path)
         except OSError:
             pass
-        inside = [r for r in rows if r[0] is not None and t0 is not None and t0 <= r[0] <= t1]
-        use = inside if inside else rows
-        if not use:
-            return None
-        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": float(max(r[2] for r in use)),
-                "reasons": sorted({n for r in use for n in r[3]}), "samples": len(use),
-                "window": "timed region" if inside else "around the timed region"}
+        return out
+
+
+def parse_clock_samples(path, dev, t0=None, t1=None):
+    """Median SM clock, maximum SM clock and the active throttle reasons of
+    the nvidia-smi samples of GPU dev in path (timestamp, index, clocks.sm,
+    clocks.max.sm, power, reasons.active, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap); the samples timestamped in [t0, t1]
+    (host epoch seconds) when there are any, else all of them."""
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    rows = []
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 10 or f[1] != str(dev):
+            continue
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        try:
+            rows.append((ts, float(f[2]), float(f[3]), [n for n, v in zip(names, f[6:10]) if v.lower() == "active"]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if r[0] is not None and t0 is not None and t0 <= r[0] <= t1]
+    use = inside if inside else rows
+    if not use:
+        return None
+    return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": float(max(r[2] for r in use)),
+            "reasons": sorted({n for r in use for n in r[3]}), "samples": len(use),
+            "window": "timed region" if inside else "around the timed region"}
 
 
 def setup_solver(csw, precision, stream, seed=3, workload="dmr", shape=None):
