@@ -10,8 +10,10 @@
 // weighted combination into modes by a fixed projection.  All of these depend
 // on geometry only, so the set-up kernel computes them in FP64 (Householder
 // QR, Cholesky) and stores one operator block per cell (Ops<K>); the
-// per-stage kernel applies them.  Smoothness-indicator sums, nonlinear weights
-// and the KXRCF threshold test are always evaluated in FP64.
+// per-stage kernel applies them.  The smoothness-indicator sums and nonlinear
+// weights are evaluated in FP64 in the FP64 and FP32-bulk modes (in float, in
+// quotient forms, in the FP32 mode); the KXRCF and positivity tests are
+// screened in the state precision and close calls recomputed in FP64.
 #include "kernels.h"
 #include "physics.cuh"
 #include "rules.cuh"
@@ -697,7 +699,7 @@ __host__ __device__ __forceinline__ void euler_eig(const R *U, R gam, R nx, R ny
     const R rho = U[0], u = U[1] / rho, v = U[2] / rho;
     const R q2 = u * u + v * v;
     const R p = (gam - R(1)) * (U[3] - R(0.5) * rho * q2);
-    const R c2 = gam * p / rho, c = rsqrt_(c2), H = (U[3] + p) / rho;
+    const R c2 = gam * p / rho, c = rsqroot(c2), H = (U[3] + p) / rho;
     const R un = u * nx + v * ny, ut = -u * ny + v * nx, b = gam - R(1);
     // columns: acoustic (-), entropy, shear, acoustic (+)
     Rm[0][0] = R(1);          Rm[0][1] = R(1);          Rm[0][2] = R(0); Rm[0][3] = R(1);
@@ -720,7 +722,7 @@ __host__ __device__ __forceinline__ void euler_eig_field(const R *U, R gam, R nx
     const R rho = U[0], u = U[1] / rho, v = U[2] / rho;
     const R q2 = u * u + v * v;
     const R p = (gam - R(1)) * (U[3] - R(0.5) * rho * q2);
-    const R c2 = gam * p / rho, c = rsqrt_(c2), H = (U[3] + p) / rho;
+    const R c2 = gam * p / rho, c = rsqroot(c2), H = (U[3] + p) / rho;
     const R un = u * nx + v * ny, ut = -u * ny + v * nx, b = gam - R(1);
     const R i2c2 = R(1) / (R(2) * c2);
     if (fl == 1) {  // entropy
@@ -1366,7 +1368,7 @@ template <typename T> __host__ __device__ inline Dual<T> operator/(Dual<T> a, Du
     const T q = a.v / b.v;
     return {q, (a.d - q * b.d) / b.v};
 }
-template <typename T> __host__ __device__ inline Dual<T> rsqrt_(Dual<T> a)
+template <typename T> __host__ __device__ inline Dual<T> rsqroot(Dual<T> a)
 {
     const T s = sqrt(a.v);
     return {s, a.d / (T(2) * s)};

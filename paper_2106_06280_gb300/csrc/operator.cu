@@ -3,9 +3,10 @@
 // the CFL reduction, the initial-condition projection, conservation sums and
 // the user-layout <-> internal-layout conversions.
 //
-// One thread per cell; within a tile of 128 Morton-ordered cells the traces
-// and the face fluxes are shared through shared memory (see k_stage), so no
-// face buffer in HBM, colouring or atomics are needed.
+// One thread per cell (owner-computes): a cell evaluates its volume integral
+// and all three face integrals, reading its neighbours' modes (Morton order
+// keeps them in L1/L2); the two cells of a face obtain exact negatives of one
+// flux (llf2), so no face buffer in HBM, colouring or atomics are needed.
 //
 // State in HBM: cell-major [cell][var][mode], coefficients of the reference-orthonormal
 // basis (u_tilde = sqrt(2/|K|) u_hat), so that
@@ -57,7 +58,7 @@ template <int EQ, typename R> __device__ __forceinline__ R mean_wave_speed(const
     const R r = m0[0] * is2, mx = m0[1] * is2, my = m0[2] * is2, E = m0[3] * is2;
     const R uu = mx / r, vv = my / r;
     const R p = (gam - R(1)) * (E - R(0.5) * (mx * uu + my * vv));
-    const R lam = rsqrt_(uu * uu + vv * vv) + rsqrt_(gam * p / r);
+    const R lam = rsqroot(uu * uu + vv * vv) + rsqroot(gam * p / r);
     return (lam >= R(0)) ? lam : R(1e30);
 }
 

@@ -7,13 +7,13 @@ namespace csw {
 
 template <typename R> __host__ __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 template <typename R> __host__ __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
-__host__ __device__ __forceinline__ float rsqrt_(float x) { return sqrtf(x); }
+__host__ __device__ __forceinline__ float rsqroot(float x) { return sqrtf(x); }
 // uncontracted products and sums (keep sign decisions identical to a plain evaluation)
 __device__ __forceinline__ float rmul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double rmul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float radd_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd_rn(double a, double b) { return __dadd_rn(a, b); }
-__host__ __device__ __forceinline__ double rsqrt_(double x) { return sqrt(x); }
+__host__ __device__ __forceinline__ double rsqroot(double x) { return sqrt(x); }
 
 // reciprocal and square root: IEEE in FP64; in FP32-bulk the hardware
 // approximations (MUFU, about 2 ulp)
