@@ -130,7 +130,9 @@ cswdg_status cswdg_project_ic(cswdg_solver *s, const double *values_host, int32_
  * CFL rule dt = cfl * min_K r_K / max_K lambda_K (r_K the inradius, lambda_K
  * the largest wave speed of the cell mean).  Steps are clipped so that t never
  * passes t_end; once t == t_end further steps do nothing.  The steps run as a
- * CUDA graph.  t_out_host (nullable) receives the time reached.
+ * CUDA graph on the solver's stream; the call waits for them once, at the end
+ * (to read the time and the error bits).  t_out_host (nullable) receives the
+ * time reached.
  * Errors: EINVAL, ENONPHYS, ECUDA. */
 cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *t_out_host);
 
