@@ -304,6 +304,24 @@ cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out_h
  * needed.  Errors: EINVAL, ECUDA. */
 cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *modes_dev, double *sums_dev);
 
+/* Host-side mesh processing alone, without a solver or a device (no
+ * counterpart in the paper; for tests and inspection): the connectivity,
+ * periodic pairing, locality order and geometry that cswdg_mesh_upload builds.
+ * degree 1 or 2; bc_kind_host: CSWDG_BC_* kind of each of the 16 face tags
+ * (as set by cswdg_set_boundary); the mesh arguments as cswdg_mesh_upload.
+ * Outputs (each nullable), in the internal cell order:
+ *   geo_host  14 x nc doubles, array-major: 2 dr/dx, 2 dr/dy, 2 ds/dx, 2 ds/dy,
+ *             then for local faces f = 0, 1, 2 the outward unit normal (x, y)
+ *             and |n~| = 2 |edge| / |cell|, then the KXRCF scale kappa;
+ *   nbr_host  3 x nc: the internal index of the neighbour across face f, or
+ *             -(boundary record + 1) for a boundary face;
+ *   nbf_host  nc: the neighbour's local face index of each face, 2 bits per face;
+ *   perm_host nc: the caller's index of each internal cell.
+ * Errors: EINVAL, EMESH (the status only; there is no solver to hold a message). */
+cswdg_status cswdg_host_mesh(int32_t degree, const int32_t *bc_kind_host, int64_t nv, const double *xy_host, int64_t nc,
+                             const int32_t *tri_host, int64_t nbf, const int32_t *bface_host, const double *period_host,
+                             double *geo_host, int32_t *nbr_host, uint8_t *nbf_host, int32_t *perm_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1144,3 +1144,30 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
 #undef STR
     return CSWDG_OK;
 }
+
+// host-side mesh processing alone, no device (see the header)
+cswdg_status cswdg_host_mesh(int32_t degree, const int32_t *bc_kind_host, int64_t nv, const double *xy_host, int64_t nc64,
+                             const int32_t *tri_host, int64_t nbf, const int32_t *bface_host, const double *period_host,
+                             double *geo_host, int32_t *nbr_host, uint8_t *nbf_host, int32_t *perm_host)
+{
+    if ((degree != 1 && degree != 2) || !bc_kind_host || !xy_host || !tri_host || nv < 3 || nc64 < 1 || nc64 > (1 << 30) ||
+        nbf < 0 || (nbf > 0 && !bface_host))
+        return CSWDG_EINVAL;
+    int32_t kinds[CSW_MAXTAG];
+    for (int t = 0; t < CSW_MAXTAG; ++t) kinds[t] = bc_kind_host[t];
+    HostMesh H;
+    if (int st = build_host_mesh(degree, kinds, nv, xy_host, nc64, tri_host, nbf, bface_host, period_host, H))
+        return (cswdg_status)st;
+    const int nc = H.nc, ld = H.ldc;
+    if (geo_host)
+        for (int g = 0; g < G_COUNT; ++g)
+            for (int c = 0; c < nc; ++c) geo_host[(size_t)g * nc + c] = H.geo[(size_t)g * ld + c];
+    if (nbr_host)
+        for (int f = 0; f < 3; ++f)
+            for (int c = 0; c < nc; ++c) nbr_host[(size_t)f * nc + c] = H.nbr[(size_t)f * ld + c];
+    if (nbf_host)
+        for (int c = 0; c < nc; ++c) nbf_host[c] = H.nbfv[c];
+    if (perm_host)
+        for (int c = 0; c < nc; ++c) perm_host[c] = H.perm[c];
+    return CSWDG_OK;
+}

@@ -66,6 +66,8 @@ def _load():
         "cswdg_stencil_operator": ([vp, i64, dp, C.POINTER(i32)], C.c_int),
         "cswdg_conservation_noalloc": ([vp, vp, vp], C.c_int),
         "cswdg_selftest_timeout": ([vp, i32], C.c_int),
+        "cswdg_host_mesh": ([i32, C.POINTER(i32), i64, dp, i64, C.POINTER(i32), i64, C.POINTER(i32), dp, dp,
+                             C.POINTER(i32), C.POINTER(C.c_uint8), C.POINTER(i32)], C.c_int),
         "cswdg_autotune": ([vp, dp, C.POINTER(i32)], C.c_int),
         "cswdg_rhs_adjoint": ([vp, C.c_double, dp, dp, dp], C.c_int),
         "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp, dp], C.c_int),
@@ -85,14 +87,39 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_launches_per_step", "cswdg_get_time",
             "cswdg_set_time", "cswdg_read_modes", "cswdg_write_modes", "cswdg_read_flags", "cswdg_num_flagged",
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
-            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_selftest_timeout", "cswdg_autotune", "cswdg_rhs_adjoint",
-            "cswdg_adjoint_steps", "cswdg_limit_adjoint",
-            "cswdg_set_stage_shape"]
+            "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_selftest_timeout",
+            "cswdg_autotune", "cswdg_rhs_adjoint", "cswdg_adjoint_steps", "cswdg_limit_adjoint",
+            "cswdg_set_stage_shape", "cswdg_host_mesh"]
 TUNE_CANDIDATES = 7
 
 
 def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def host_mesh(problem, degree):
+    """Connectivity, locality order and geometry of a workloads.Problem as the
+    library builds them on the host (no device): dict of geo (14, nc), nbr
+    (3, nc), nbf (nc,), perm (nc,), all in the internal cell order."""
+    m = problem.mesh
+    kinds = np.zeros(16, dtype=np.int32)
+    for tag, (kind, _) in problem.boundaries.items():
+        kinds[tag] = kind
+    xy = _d(m.xy)
+    tri = np.ascontiguousarray(m.tri, dtype=np.int32)
+    bface = np.ascontiguousarray(m.bface, dtype=np.int32)
+    per = None if m.period is None else _d(m.period)
+    nc = tri.shape[0]
+    geo = np.zeros((14, nc))
+    nbr = np.zeros((3, nc), dtype=np.int32)
+    nbf = np.zeros(nc, dtype=np.uint8)
+    perm = np.zeros(nc, dtype=np.int32)
+    st = lib.cswdg_host_mesh(degree, _p(kinds, C.c_int32), xy.shape[0], _p(xy), nc, _p(tri, C.c_int32), bface.shape[0],
+                             _p(bface, C.c_int32), None if per is None else _p(per), _p(geo), _p(nbr, C.c_int32),
+                             _p(nbf, C.c_uint8), _p(perm, C.c_int32))
+    if st != OK:
+        raise CswdgError(st, "host mesh processing failed")
+    return {"geo": geo, "nbr": nbr, "nbf": nbf, "perm": perm}
 
 
 def _p(a, ctype=C.c_double):
