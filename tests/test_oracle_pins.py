@@ -577,3 +577,44 @@ def test_convergence_euler_entropy_wave(k, limiter, order):
     Measured on 8/16/32 meshes at t = 0.05: 1.95 (P1) and 2.80 (P2)."""
     e = _entropy_wave_errors(k, limiter, [8, 16, 32])
     assert np.log2(e[-2] / e[-1]) > order, e
+
+
+def test_dmr_boundaries_follow_the_exact_shock_position():
+    """Sec. 4.2 Example 5 boundaries (reading R-bc) against the closed form of
+    the shock position: with the post-shock state everywhere, the operator
+    vanishes in every cell whose ghosts equal that state (left and bottom
+    x < 1/6 inflow, right outflow, top boundary left of the Mach-10 front at
+    x_s(t) = 1/6 + (1 + 20 t)/sqrt(3)) and not in the cells on the top boundary
+    right of the front (pre-shock ghost) nor on the reflecting wall (the
+    post-shock flow crosses it)."""
+    pb = W.double_mach(48, 12, seed=3)
+    m = pb.mesh
+    post = np.array(pb.boundaries[1][1], dtype=float)
+    o = oracle.Oracle(pb, k=1, limiter=0)
+    u = o.project(lambda x, y: np.tile(post, (len(x), 1)))
+    t = 0.05
+    r = np.abs(o.rhs(u, t)).reshape(m.nc, -1).max(axis=1)
+    xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / np.sqrt(3.0)
+    cell_of = {}
+    for c, tri in enumerate(m.tri):
+        for a, b in ((tri[0], tri[1]), (tri[1], tri[2]), (tri[2], tri[0])):
+            cell_of[(min(a, b), max(a, b))] = c
+    expect = np.zeros(m.nc, dtype=int)  # 0 zero residual, 1 nonzero, -1 not classified
+    h = 4.0 / 48
+    for v0, v1, tag in m.bface:
+        c = cell_of[(min(v0, v1), max(v0, v1))]
+        xa, xb = sorted((m.xy[v0, 0], m.xy[v1, 0]))
+        if tag == 2:
+            kind = 1
+        elif tag == 4:
+            kind = 0 if xb < xs - 0.1 * h else (1 if xa > xs + 0.1 * h else -1)
+        else:
+            kind = 0
+        if kind == -1 or expect[c] == -1:
+            expect[c] = -1
+        else:
+            expect[c] = max(expect[c], kind)
+    big = r.max()
+    assert (expect == 1).sum() > 20 and (expect == 0).sum() > m.nc // 2
+    assert np.all(r[expect == 0] < 1e-10 * big), r[expect == 0].max() / big
+    assert np.all(r[expect == 1] > 1e-3 * big), r[expect == 1].min() / big
