@@ -10,6 +10,8 @@ the CPU: the properties the stage kernel relies on.
 * The internal order is a permutation of the caller's cells, and the cell
   geometry matches the caller's triangle it came from.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -73,8 +75,15 @@ def test_host_mesh_faces_and_normals(cswdg, name, pb, k):
 
 def test_host_mesh_rejects_bad_arguments(cswdg):
     pb = W.burgers_sine(4, seed=1)
-    with pytest.raises(cswdg.CswdgError):
+    with pytest.raises(cswdg.CswdgError, match="EINVAL"):
         cswdg.host_mesh(pb, 3)  # no such degree
+    # a clockwise triangle is a mesh error, reported as a status
+    tri = pb.mesh.tri.copy()
+    tri[0] = tri[0][[0, 2, 1]]
+    mesh = dataclasses.replace(pb.mesh, tri=tri)
+    bad = dataclasses.replace(pb, mesh=mesh)
+    with pytest.raises(cswdg.CswdgError, match="EMESH"):
+        cswdg.host_mesh(bad, 2)
 
 
 def test_morton_order_keeps_neighbours_close(cswdg):
