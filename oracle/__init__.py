@@ -22,12 +22,17 @@ _bp = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction: same bits on x86 and Arm)."""
+    """Compile the oracle with gcc (no FMA contraction: same bits on x86 and Arm).
+
+    OpenMP spreads the independent per-cell loops (operator, detection,
+    reconstruction) over the host cores; every cell is computed by one thread
+    from read-only inputs, so the results do not depend on the thread count.
+    """
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+                               "-ffp-contract=off", "-fopenmp", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -252,13 +257,13 @@ class Oracle:
         return out.reshape(3, 7, self.nvar)
 
     def weno(self, c, ubar0, thirds, halves=None, force_linear=False):
-        info = np.zeros(33)
+        info = np.zeros(40)
         modes = np.zeros(self.np)
         hf = None if halves is None else _f64(halves).ravel()
         st = lib().or_hook_weno(self.h, c, ubar0, _f64(thirds).ravel(), None if hf is None else hf.ctypes.data,
                                 int(force_linear), info, modes)
         return dict(q2=info[0:2], q3=info[2:7], q4=info[7:16], gamma=info[21:25], beta=info[25:29],
-                    omega=info[29:33], modes=modes, status=st)
+                    omega=info[29:33], beta1l=info[33:36], sigma=info[36:39], tau=info[39], modes=modes, status=st)
 
     def beta(self, c, coef, deg):
         coef = _f64(coef)

@@ -711,6 +711,7 @@ static void rhs_cell(const Oracle *o, const double *u, double t, int c, double *
 
 void or_rhs(const Oracle *o, const double *u, double t, double *L)
 {
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int c = 0; c < o->nc; ++c) rhs_cell(o, u, t, c, L + (size_t)c * o->nvar * o->np);
 }
 
@@ -725,9 +726,16 @@ void or_rhs_cells(const Oracle *o, const double *u, double t, int n, const int *
  * Readings R-kxrcf: inflow faces are those with vbar.n < 0, vbar from the
  * cell mean ((f'(u), g'(u)) = (u,u) for Burgers, the velocity for Euler);
  * the indicator variable is u (Burgers) or the density (Euler); ||U_j|| is
- * the L2 norm over the cell, sqrt(sum_m u_m^2) in the orthonormal basis; h is
- * the circumradius; no inflow face gives R = 0; ||U_j|| = 0 flags the cell
- * only if the jump integral is non-zero; troubled iff R > C_K.
+ * the L2 norm over the cell taken with respect to the cell's normalised
+ * measure, (|K|^{-1} int_K U^2)^{1/2} = sqrt(sum_m u_m^2 / |K|) in the
+ * orthonormal basis.  The un-normalised norm carries a factor |K|^{1/2} ~ h,
+ * so R would not vanish on smooth P1 data (numerator O(h^{k+2}), denominator
+ * O(h^{(k+1)/2} h h)) and the fixed threshold C_K = 1 of the cited KXRCF
+ * indicator would flag smooth cells at every resolution; with the normalised
+ * norm R = O(h^{(k+1)/2}) on smooth data and O(h^{-(k+1)/2}) at a jump, as
+ * the indicator is designed.  h is the circumradius; no inflow face gives
+ * R = 0; ||U_j|| = 0 flags the cell only if the jump integral is non-zero;
+ * troubled iff R > C_K.
  * ====================================================================== */
 
 static double circumradius(const Tri *t)
@@ -770,7 +778,7 @@ static int detect_cell(const Oracle *o, const double *u, double t, int c, double
         double a = u[(size_t)(c * nv + 0) * np + m];
         nrm += a * a;
     }
-    nrm = sqrt(nrm);
+    nrm = sqrt(nrm / area);
     double h = circumradius(&tc);
     double hp = (o->k == 1) ? h : h * sqrt(h); /* h^{(k+1)/2} */
     double R;
@@ -783,6 +791,7 @@ static int detect_cell(const Oracle *o, const double *u, double t, int c, double
 
 void or_detect(const Oracle *o, const double *u, double t, unsigned char *flags, double *R)
 {
+    #pragma omp parallel for schedule(dynamic, 64)
     for (int c = 0; c < o->nc; ++c) flags[c] = (unsigned char)detect_cell(o, u, t, c, R ? R + c : NULL);
 }
 
@@ -1020,6 +1029,7 @@ typedef struct {
     double q2[2], q3[5], q4[9];   /* least-squares coefficients */
     double gam[5];                /* linear weights of the final combination */
     double beta[4], omega[4];
+    double beta1l[3], sigma[3], tau; /* beta_{1,l}, sigma_l (Eq. sigmaEqn) and tau */
     int nslot;
     double modes[OR_MAXNP];       /* reconstructed modes 1..np-1 (mode 0 untouched) */
     int status;
@@ -1093,23 +1103,42 @@ static void weno_scalar(const Oracle *o, const Frame *F, const Stencil *S, doubl
         bl[f] = (m11 * r2 - m21 * r1) / det;
         b11[f] = F->area * (al[f] * al[f] + bl[f] * bl[f]);
     }
-    double D = (fabs(b11[0] - b11[1]) * fabs(b11[0] - b11[1]) + fabs(b11[1] - b11[2]) * fabs(b11[1] - b11[2]) +
-                fabs(b11[2] - b11[0]) * fabs(b11[2] - b11[0])) / 3.0;
+    /* Eq. sigmaEqn (reading R-sigma): the printed numerator squares each
+     * difference inside an already squared mean; taken as the [zs4] form the
+     * paper cites for this magnification, the square of the mean absolute
+     * difference, sigma_l = (1/3) (1 + D^2 / (beta_{1,l} + eps)),
+     * D = (|b11 - b12| + |b12 - b13| + |b13 - b11|) / 3. */
+    double D = (fabs(b11[0] - b11[1]) + fabs(b11[1] - b11[2]) + fabs(b11[2] - b11[0])) / 3.0;
     double sig[3], sigsum = 0.0;
     for (int f = 0; f < 3; ++f) { sig[f] = (1.0 / 3.0) * (1.0 + D * D / (b11[f] + OR_EPS)); sigsum += sig[f]; }
+    for (int f = 0; f < 3; ++f) { W->beta1l[f] = b11[f]; W->sigma[f] = sig[f]; }
     double abar = 0.0, bbar = 0.0;
     for (int f = 0; f < 3; ++f) { abar += sig[f] / sigsum * al[f]; bbar += sig[f] / sigsum * bl[f]; }
     W->beta[0] = F->area * (abar * abar + bbar * bbar);
     W->beta[1] = beta_poly(F, &o->duf4, 2, p2, 1);
     W->beta[2] = beta_poly(F, &o->duf4, 5, p3, 2);
     if (k == 2) W->beta[3] = beta_poly(F, &o->duf4, 9, p4, 3);
-    /* Step 4: tau and nonlinear weights (Eqs. tauNonlinearWeightsP1/P2, nonLinearWeightsP1/P2) */
+    /* Step 4: tau and nonlinear weights (Eqs. tauNonlinearWeightsP1/P2,
+     * nonLinearWeightsP1/P2), reading R-weno: the paper takes these weights
+     * from the WENO-Z recipe of [ccd], whose tau is built from absolute
+     * differences of the smoothness indicators (linear in beta, so tau/beta
+     * does not change when the data are scaled) and whose ratio tau/(eps+beta)
+     * carries a power p.  tau is the mean absolute difference between the top
+     * slot's beta and the others', and p = k + 1: with the paper's linear
+     * weights gamma_{l,m} = O(h^{m-l}) this is the smallest power for which a
+     * non-smooth top stencil drops out to O(h^{k+1}) against a smooth T1
+     * (omega_top ~ h^{2p-(k+1)}), the order reduction Step 4 states. */
     double tau;
-    if (k == 1) tau = (fabs(W->beta[2] - W->beta[0]) * fabs(W->beta[2] - W->beta[0]) + fabs(W->beta[2] - W->beta[1]) * fabs(W->beta[2] - W->beta[1])) / 4.0;
-    else tau = (fabs(W->beta[3] - W->beta[0]) * fabs(W->beta[3] - W->beta[0]) + fabs(W->beta[3] - W->beta[1]) * fabs(W->beta[3] - W->beta[1]) +
-                fabs(W->beta[3] - W->beta[2]) * fabs(W->beta[3] - W->beta[2])) / 16.0;
+    if (k == 1) tau = (fabs(W->beta[2] - W->beta[0]) + fabs(W->beta[2] - W->beta[1])) / 2.0;
+    else tau = (fabs(W->beta[3] - W->beta[0]) + fabs(W->beta[3] - W->beta[1]) + fabs(W->beta[3] - W->beta[2])) / 3.0;
+    W->tau = tau;
     double wsum = 0.0, wb[4];
-    for (int l = 0; l < nslot; ++l) { wb[l] = W->gam[l] * (1.0 + tau / (OR_EPS + W->beta[l])); wsum += wb[l]; }
+    for (int l = 0; l < nslot; ++l) {
+        double r = tau / (OR_EPS + W->beta[l]), rp = r;
+        for (int e = 1; e < k + 1; ++e) rp *= r; /* (tau / (eps + beta_l))^{k+1} */
+        wb[l] = W->gam[l] * (1.0 + rp);
+        wsum += wb[l];
+    }
     for (int l = 0; l < nslot; ++l) W->omega[l] = force_linear ? W->gam[l] : wb[l] / wsum;
     /* Eq. WENOApprox...: u_q = sum_l omega_l p_l(x_q) at the reconstruction points */
     double zero[14] = {0};
@@ -1271,6 +1300,7 @@ int or_limit(const Oracle *o, const double *u_in, double t, double *u_out, unsig
     size_t n = (size_t)o->nc * o->nvar * o->np;
     memcpy(u_out, u_in, sizeof(double) * n);
     int status = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(min : status)
     for (int c = 0; c < o->nc; ++c) {
         int fl = 0;
         if (o->limiter == LIM_ALL) fl = 1;
@@ -1537,6 +1567,9 @@ int or_hook_weno(const Oracle *o, int c, double ubar0, const double *th_in, cons
     for (int j = 0; j < 4; ++j) info[p++] = W.gam[j];
     for (int j = 0; j < 4; ++j) info[p++] = W.beta[j];
     for (int j = 0; j < 4; ++j) info[p++] = W.omega[j];
+    for (int j = 0; j < 3; ++j) info[p++] = W.beta1l[j];
+    for (int j = 0; j < 3; ++j) info[p++] = W.sigma[j];
+    info[p++] = W.tau;
     modes[0] = ubar0 * sqrt(F.area);
     for (int i = 1; i < o->np; ++i) modes[i] = W.modes[i];
     return W.status;

@@ -40,7 +40,7 @@ def test_two_replicas_max_time_and_whole_job_rate():
     import torch.multiprocessing as mp
 
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:  # no fork after the oracle's threads exist
         out = mgr.dict()
         mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
         r0, r1 = out[0], out[1]
