@@ -131,8 +131,11 @@ cswdg_status cswdg_project_ic(cswdg_solver *s, const double *values_host, int32_
  * the largest wave speed of the cell mean).  Steps are clipped so that t never
  * passes t_end; once t == t_end further steps do nothing.  The steps run as a
  * CUDA graph on the solver's stream; the call waits for them once, at the end
- * (to read the time and the error bits).  t_out_host (nullable) receives the
- * time reached.
+ * (to read the time and the error bits).  With a finite t_end (< 1e299) and
+ * more than 256 steps, the steps are launched 256 at a time and the call also
+ * reads the time after each batch, returning once t_end is reached or an error
+ * bit is set, so a large nsteps may stand for "until t_end".  t_out_host
+ * (nullable) receives the time reached.
  * Errors: EINVAL, ENONPHYS, ECUDA. */
 cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end, double *t_out_host);
 
@@ -295,9 +298,13 @@ cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out_h
  * reduction's scratch is one fixed device array inside the library (2 MiB on
  * every GPU that loads it, held until the process exits), so the call allocates
  * nothing: no cudaMalloc, cudaFree or allocating library call.  Limit: at most
- * 16,777,216 cells (larger meshes get CSWDG_EINVAL).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  All calls share the array: two calls whose
+ * 16,777,216 cells (larger meshes get CSWDG_EINVAL).  The work runs on the
+ * solver's device (the one current when its mesh was uploaded), whichever
+ * device is current at the call; the call makes it current for its duration
+ * and restores the caller's device.  The first call for a device looks up the
+ * array's device address there (cudaGetSymbolAddress, once per device, safe
+ * from several host threads); make that first call before any stream capture.
+ * All calls share the array: two calls whose
  * work overlaps on the GPU (different streams, or different solvers on the
  * same device at the same time) race; calls queued on one stream do not.
  * Every call rewrites the part of the scratch it reads, so no clearing is

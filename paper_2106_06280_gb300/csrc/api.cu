@@ -24,6 +24,7 @@ struct cswdg_solver {
     cswdg_config cfg{};
     int nv = 1, np = 3, k = 1, eq = 0, fp32 = 0, w32 = 0;
     cudaStream_t stream = nullptr;
+    int device = -1;  // the device that holds the solver's memory (current at mesh upload)
     std::string err;
     BcTab bc{};
     bool mesh_ready = false;
@@ -311,9 +312,11 @@ cswdg_status download_modes(cswdg_solver *s, const void *src, double *modes, boo
 }  // namespace
 
 namespace csw {
-bool solver_view(const cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area, void **stream)
+bool solver_view(const cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area, void **stream,
+                 int *device)
 {
     if (!s || !s->mesh_ready) return false;
+    *device = s->device;
     *nc = s->nc;
     *ldc = s->ldc;
     *nvar = s->nv;
@@ -428,6 +431,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     const size_t nstate = (size_t)s->nv * s->np * ld;
     cudaError_t e = cudaSuccess;
     auto A_ = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A_(cudaGetDevice(&s->device));
     A_(cudaMalloc(&s->U, nstate * rs));
     A_(cudaMalloc(&s->A, nstate * rs));
     A_(cudaMalloc(&s->B, nstate * rs));
@@ -598,8 +602,20 @@ cswdg_status cswdg_step(cswdg_solver *s, double dt, int64_t nsteps, double t_end
         s->lam_stale = false;
     }
     if (cswdg_status r = get_graph(s, use_cfl)) return r;
-    for (int64_t i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(s->graph[use_cfl], s->stream));
+    // long runs towards a finite t_end: launch in chunks and stop once the device time
+    // has reached t_end (steps past t_end do nothing, but each still launches)
+    constexpr int64_t kChunk = 256;
     Ctl h;
+    int64_t done = 0;
+    while (done < nsteps) {
+        const int64_t n = (t_end < 1e299 && nsteps - done > kChunk) ? kChunk : nsteps - done;
+        for (int64_t i = 0; i < n; ++i) CK(cudaGraphLaunch(s->graph[use_cfl], s->stream));
+        done += n;
+        if (done < nsteps) {
+            if (cswdg_status r = read_ctl(s, &h)) return r;
+            if (h.err || !(h.t_next < t_end)) break;
+        }
+    }
     if (cswdg_status r = read_ctl(s, &h)) return r;
     h.t = h.t_next;
     if (t_out) *t_out = h.t_next;

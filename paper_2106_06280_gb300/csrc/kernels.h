@@ -70,7 +70,7 @@ template <typename R> void launch_axpby(size_t n, R a, const R *x, R b, const R 
 
 // read-only view of a solver for entry points outside api.cu (false: no mesh)
 bool solver_view(const struct ::cswdg_solver *s, int *nc, int *ldc, int *nvar, int *np, int *fp32, const double **area,
-                 void **stream);
+                 void **stream, int *device);
 // record an error on the solver and return the status
 cswdg_status solver_fail(struct ::cswdg_solver *s, cswdg_status st, const char *fmt, ...);
 

@@ -607,8 +607,8 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
                 b1[f] = al[f] * al[f] + bl[f] * bl[f];  // beta_{1,l}
                 e[f] = b1[f] + W(eps);
             }
-            const W d01 = fabs(b1[0] - b1[1]), d12 = fabs(b1[1] - b1[2]), d20 = fabs(b1[2] - b1[0]);
-            const W D = (d01 * d01 + d12 * d12 + d20 * d20) * W(1.0 / 3.0);  // a product: a double division is slow on this FP64 pipe
+            // D: mean absolute difference of the beta_{1,l} (reading R-sigma)
+            const W D = (fabs(b1[0] - b1[1]) + fabs(b1[1] - b1[2]) + fabs(b1[2] - b1[0])) * W(1.0 / 3.0);  // a product: a double division is slow on this FP64 pipe
             const W D2 = D * D;
             // sigma_l is proportional to (e_l + D^2) / e_l; multiply through by e_0 e_1 e_2
             const W w0 = (e[0] + D2) * e[1] * e[2], w1 = (e[1] + D2) * e[0] * e[2], w2 = (e[2] + D2) * e[0] * e[1];
@@ -616,21 +616,25 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
             const W ab = (w0 * al[0] + w1 * al[1] + w2 * al[2]) * inv, bb = (w0 * bl[0] + w1 * bl[1] + w2 * bl[2]) * inv;
             beta[0] = ab * ab + bb * bb;
         }
-        // Step 4: tau and nonlinear weights, normalised over a common denominator
+        // Step 4 (reading R-weno): tau the mean absolute difference to the top slot's beta,
+        // omega_l proportional to gamma_l (1 + (tau / a_l)^(K+1)), a_l = eps + beta_l, formed
+        // over the common denominator prod_m a_m^(K+1) (one reciprocal; in double every
+        // factor stays in range: a^12 >= 1e-120)
         if (K == 1) {
-            const W e1 = fabs(beta[2] - beta[0]), e2 = fabs(beta[2] - beta[1]);
-            const W tau = (e1 * e1 + e2 * e2) * 0.25;
+            const W tau = (fabs(beta[2] - beta[0]) + fabs(beta[2] - beta[1])) * W(0.5);
             const W a0 = eps + beta[0], a1 = eps + beta[1], a2 = eps + beta[2];
-            const W w0 = (W)gm[0] * (a0 + tau) * a1 * a2, w1 = (W)gm[1] * (a1 + tau) * a0 * a2, w2 = (W)gm[2] * (a2 + tau) * a0 * a1;
+            const W s0 = a0 * a0, s1 = a1 * a1, s2 = a2 * a2, t2 = tau * tau;
+            const W w0 = (W)gm[0] * (s0 + t2) * s1 * s2, w1 = (W)gm[1] * (s1 + t2) * s0 * s2, w2 = (W)gm[2] * (s2 + t2) * s0 * s1;
             const W inv = wrcp(w0 + w1 + w2);
             om[0] = w0 * inv; om[1] = w1 * inv; om[2] = w2 * inv; om[3] = W(0);
         } else {
-            const W e1 = fabs(beta[3] - beta[0]), e2 = fabs(beta[3] - beta[1]), e3 = fabs(beta[3] - beta[2]);
-            const W tau = (e1 * e1 + e2 * e2 + e3 * e3) * 0.0625;
-            const W a[4] = {eps + beta[0], eps + beta[1], eps + beta[2], eps + beta[3]};
-            const W p01 = a[0] * a[1], p23 = a[2] * a[3];
-            const W w[4] = {(W)gm[3] * (a[0] + tau) * a[1] * p23, (W)gm[4] * (a[1] + tau) * a[0] * p23,
-                            (W)gm[5] * (a[2] + tau) * p01 * a[3], (W)gm[6] * (a[3] + tau) * p01 * a[2]};
+            const W tau = (fabs(beta[3] - beta[0]) + fabs(beta[3] - beta[1]) + fabs(beta[3] - beta[2])) * W(1.0 / 3.0);
+            const W t3 = tau * tau * tau;
+            W c[4];
+            for (int l = 0; l < 4; ++l) { const W al_ = eps + beta[l]; c[l] = al_ * al_ * al_; }
+            const W p01 = c[0] * c[1], p23 = c[2] * c[3];
+            const W w[4] = {(W)gm[3] * (c[0] + t3) * c[1] * p23, (W)gm[4] * (c[1] + t3) * c[0] * p23,
+                            (W)gm[5] * (c[2] + t3) * p01 * c[3], (W)gm[6] * (c[3] + t3) * p01 * c[2]};
             const W inv = wrcp(w[0] + w[1] + w[2] + w[3]);
             for (int l = 0; l < 4; ++l) om[l] = w[l] * inv;
         }
@@ -648,8 +652,7 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
                 b1[f] = al[f] * al[f] + bl[f] * bl[f];
                 ie[f] = rrcp(b1[f] + R(eps));
             }
-            const R d01 = b1[0] - b1[1], d12 = b1[1] - b1[2], d20 = b1[2] - b1[0];
-            const R D = (d01 * d01 + d12 * d12 + d20 * d20) * R(1.0 / 3.0);
+            const R D = (rabs(b1[0] - b1[1]) + rabs(b1[1] - b1[2]) + rabs(b1[2] - b1[0])) * R(1.0 / 3.0);
             R s[3];
             if (D >= R(1)) {
                 const R iD = rrcp(D), iD2 = iD * iD;
@@ -664,18 +667,29 @@ __host__ __device__ __forceinline__ void weno_field(const R *__restrict__ op, co
         }
         constexpr int NL = (K == 1) ? 3 : 4;
         R tau = R(0);
-        for (int l = 0; l < NL - 1; ++l) {
-            const R e = beta[NL - 1] - beta[l];
-            tau += e * e;
-        }
-        tau *= (K == 1) ? R(0.25) : R(1.0 / 16.0);
+        for (int l = 0; l < NL - 1; ++l) tau += rabs(beta[NL - 1] - beta[l]);
+        tau *= (K == 1) ? R(0.5) : R(1.0 / 3.0);
         const R *gl = gm + ((K == 1) ? 0 : 3);
+        // (tau / a)^(K+1) with a >= eps: when tau >= 1 every weight is divided by
+        // tau^(K+1) first, so no term exceeds eps^-(K+1) = 1e30 (float range 3e38)
         R w[NL], wsum = R(0);
         if (tau >= R(1)) {
             const R it = rrcp(tau);
-            for (int l = 0; l < NL; ++l) w[l] = gl[l] * (it + rrcp(beta[l] + R(eps)));
+            R itp = it;
+            for (int e = 0; e < K; ++e) itp *= it;
+            for (int l = 0; l < NL; ++l) {
+                const R ia = rrcp(beta[l] + R(eps));
+                R iap = ia;
+                for (int e = 0; e < K; ++e) iap *= ia;
+                w[l] = gl[l] * (itp + iap);
+            }
         } else {
-            for (int l = 0; l < NL; ++l) w[l] = gl[l] * (R(1) + tau * rrcp(beta[l] + R(eps)));
+            for (int l = 0; l < NL; ++l) {
+                const R r = tau * rrcp(beta[l] + R(eps));
+                R rp = r;
+                for (int e = 0; e < K; ++e) rp *= r;
+                w[l] = gl[l] * (R(1) + rp);
+            }
         }
         for (int l = 0; l < NL; ++l) wsum += w[l];
         const R inv = rrcp(wsum);
@@ -1446,8 +1460,12 @@ __device__ __forceinline__ void weno_field_vjp(const R *__restrict__ op, const R
         b1[f] = al[f] * al[f] + bl[f] * bl[f];
         e[f] = b1[f] + eps;
     }
+    // D: mean absolute difference of the beta_{1,l} (reading R-sigma); sgn: its derivative
     const W d01 = b1[0] - b1[1], d12 = b1[1] - b1[2], d20 = b1[2] - b1[0];
-    const W D = (d01 * d01 + d12 * d12 + d20 * d20) / W(3), D2 = D * D;
+    const W s01 = (d01 > W(0)) ? W(1) : ((d01 < W(0)) ? W(-1) : W(0));
+    const W s12 = (d12 > W(0)) ? W(1) : ((d12 < W(0)) ? W(-1) : W(0));
+    const W s20 = (d20 > W(0)) ? W(1) : ((d20 < W(0)) ? W(-1) : W(0));
+    const W D = (fabs(d01) + fabs(d12) + fabs(d20)) / W(3), D2 = D * D;
     W sg[3], Ss = W(0);
     for (int f = 0; f < 3; ++f) { sg[f] = W(1) + D2 / e[f]; Ss += sg[f]; }
     W ab = W(0), bb = W(0);
@@ -1455,15 +1473,29 @@ __device__ __forceinline__ void weno_field_vjp(const R *__restrict__ op, const R
     ab /= Ss;
     bb /= Ss;
     beta[0] = ab * ab + bb * bb;
-    // ---- Step 4 tau and weights (quotient form) ----
-    const W ctau = (K == 1) ? W(0.25) : W(1.0 / 16.0);
-    W tau = W(0);
-    for (int l = 0; l < NL - 1; ++l) { const W d = beta[NL - 1] - beta[l]; tau += d * d; }
+    // ---- Step 4 tau and weights (reading R-weno), in double whatever W: the ratio's
+    // power K+1 and its derivative (tau / a)^(K+1) / a reach 1e40 when a beta vanishes ----
+    constexpr int PW = K + 1;
+    const double ctau = (K == 1) ? 0.5 : 1.0 / 3.0;
+    double tau = 0.0, sgn[3];
+    for (int l = 0; l < NL - 1; ++l) {
+        const double d = (double)beta[NL - 1] - (double)beta[l];
+        sgn[l] = (d > 0.0) ? 1.0 : ((d < 0.0) ? -1.0 : 0.0);
+        tau += fabs(d);
+    }
     tau *= ctau;
     const R *gl = gm + ((K == 1) ? 0 : 3);
-    W a[4], z[4], om[4], Sz = W(0);
-    for (int l = 0; l < NL; ++l) { a[l] = eps + beta[l]; z[l] = (W)gl[l] * (W(1) + tau / a[l]); Sz += z[l]; }
-    for (int l = 0; l < NL; ++l) om[l] = z[l] / Sz;
+    double a[4], rp[4], z[4], Sz = 0.0;
+    W om[4];
+    for (int l = 0; l < NL; ++l) {
+        a[l] = 1e-10 + (double)beta[l];
+        const double r = tau / a[l];
+        rp[l] = r;
+        for (int e = 1; e < PW; ++e) rp[l] *= r;  // (tau / a_l)^(K+1)
+        z[l] = (double)gl[l] * (1.0 + rp[l]);
+        Sz += z[l];
+    }
+    for (int l = 0; l < NL; ++l) om[l] = (W)(z[l] / Sz);
     // ---- reverse: Step 5 projection ----
     W cmb[NM];
     for (int j = 0; j < NM; ++j) {
@@ -1479,20 +1511,23 @@ __device__ __forceinline__ void weno_field_vjp(const R *__restrict__ op, const R
         for (int j = 0; j < NM; ++j) { s += cmb[j] * p[l - 1][j]; pb[l - 1][j] = om[l] * cmb[j]; }
         omb[l] = s;
     }
-    // ---- Step 4 reverse ----
-    W dot = W(0);
-    for (int l = 0; l < NL; ++l) dot += omb[l] * om[l];
-    W betab[4] = {W(0), W(0), W(0), W(0)}, taub = W(0);
+    // ---- Step 4 reverse: z_l = gamma_l (1 + (tau/a_l)^P), d z_l/d tau = gamma_l P (tau/a_l)^P / tau,
+    // d z_l/d a_l = -gamma_l P (tau/a_l)^P / a_l ----
+    double dot = 0.0;
+    for (int l = 0; l < NL; ++l) dot += (double)omb[l] * (double)om[l];
+    double betabd[4] = {0.0, 0.0, 0.0, 0.0}, taub = 0.0;
     for (int l = 0; l < NL; ++l) {
-        const W zb = (omb[l] - dot) / Sz;
-        taub += zb * (W)gl[l] / a[l];
-        betab[l] += -zb * (W)gl[l] * tau / (a[l] * a[l]);
+        const double zb = ((double)omb[l] - dot) / Sz;
+        const double g = zb * (double)gl[l] * PW * rp[l];
+        if (tau > 0.0) taub += g / tau;
+        betabd[l] -= g / a[l];
     }
     for (int l = 0; l < NL - 1; ++l) {
-        const W d = beta[NL - 1] - beta[l];
-        betab[l] -= W(2) * ctau * d * taub;
-        betab[NL - 1] += W(2) * ctau * d * taub;
+        betabd[l] -= ctau * sgn[l] * taub;
+        betabd[NL - 1] += ctau * sgn[l] * taub;
     }
+    W betab[4];
+    for (int l = 0; l < 4; ++l) betab[l] = (W)betabd[l];
     // ---- Step 3 reverse: beta_l = |L^T p|^2 -> p_b += 2 beta_b L y ----
     for (int l = 0; l < NL - 1; ++l)
         for (int i = 0; i < nn[l]; ++i) {
@@ -1512,9 +1547,9 @@ __device__ __forceinline__ void weno_field_vjp(const R *__restrict__ op, const R
         W D2b = W(0);
         for (int f = 0; f < 3; ++f) { b1b[f] = -sgb[f] * D2 / (e[f] * e[f]); D2b += sgb[f] / e[f]; }
         const W Db = W(2) * D * D2b;
-        b1b[0] += Db * (W(2) * d01 - W(2) * d20) / W(3);
-        b1b[1] += Db * (W(2) * d12 - W(2) * d01) / W(3);
-        b1b[2] += Db * (W(2) * d20 - W(2) * d12) / W(3);
+        b1b[0] += Db * (s01 - s20) / W(3);
+        b1b[1] += Db * (s12 - s01) / W(3);
+        b1b[2] += Db * (s20 - s12) / W(3);
         for (int f = 0; f < 3; ++f) {
             alb[f] += W(2) * al[f] * b1b[f];
             blb[f] += W(2) * bl[f] * b1b[f];

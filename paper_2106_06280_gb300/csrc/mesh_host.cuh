@@ -199,7 +199,9 @@ inline int build_host_mesh(int k, const int32_t *bckind, int64_t nv, const doubl
             geo[(G_N0L + 3 * f) * ld + i] = 2.0 * len[f] / K;
         }
         const double hc = len[0] * len[1] * len[2] / (4.0 * K);
-        geo[G_KAPPA * ld + i] = ((k == 1) ? hc : hc * std::sqrt(hc)) * std::sqrt(0.5 * K);
+        // KXRCF denominator factor h^{(k+1)/2} ||.||: the cell's L2 norm over its normalised
+        // measure is sqrt(sum u~_m^2 / 2) for the stored coefficients u~ = sqrt(2/|K|) u^
+        geo[G_KAPPA * ld + i] = ((k == 1) ? hc : hc * std::sqrt(hc)) * std::sqrt(0.5);
         scv[i] = std::sqrt(2.0 / K);
         arv[i] = K;
         rmin = std::min(rmin, 2.0 * K / per_);

@@ -14,7 +14,10 @@
 //                   - sum_faces |n~| sum_g w_g psi_i(r_g) F*(u-, u+; n),
 // with G = 2 (dr/dx, dr/dy, ds/dx, ds/dy), n the outward unit normal and
 // |n~| = 2 |e| / |K|.
+#include <mutex>
+
 #include "../../include/cswdg.h"
+#include "noalloc_limits.h"
 #include "kernels.h"
 #include "physics.cuh"
 #include "tables.cuh"
@@ -530,44 +533,59 @@ template void launch_conservation<double>(int, int, int, int, const double *, co
 // file-scope device array instead of a buffer allocated per solver; every GPU
 // that loads the library holds it (2 MiB) until the process exits.
 // ---------------------------------------------------------------------------
-#define CSW_NOALLOC_MAX_BLOCKS 65536  // 256 cells per block: at most 16,777,216 cells
-#define CSW_NOALLOC_MAX_VARS 4
 static __device__ __align__(256) double g_noalloc_partial[CSW_NOALLOC_MAX_BLOCKS * CSW_NOALLOC_MAX_VARS];
 
 namespace {
 constexpr int kMaxDevices = 64;
+// device address of g_noalloc_partial on each device, looked up once per device
+std::once_flag g_noalloc_once[kMaxDevices];
 double *g_noalloc_ptr[kMaxDevices] = {nullptr};
+cudaError_t g_noalloc_err[kMaxDevices] = {cudaSuccess};
+
+// makes `dev` current for the lifetime of the guard and restores the caller's device
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+        else if (err == cudaSuccess) prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 }  // namespace
 
 extern "C" cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *modes_dev, double *sums_dev)
 {
-    int nc = 0, ld = 0, nv = 0, np = 0, fp32 = 0;
+    int nc = 0, ld = 0, nv = 0, np = 0, fp32 = 0, dev = -1;
     const double *area = nullptr;
     cudaStream_t st = nullptr;
-    if (!csw::solver_view(s, &nc, &ld, &nv, &np, &fp32, &area, (void **)&st) || !modes_dev || !sums_dev)
+    if (!csw::solver_view(s, &nc, &ld, &nv, &np, &fp32, &area, (void **)&st, &dev) || !modes_dev || !sums_dev)
         return csw::solver_fail(s, CSWDG_EINVAL, "conservation_noalloc: no mesh or null pointer");
-    const int nblk = (nc + 255) / 256;
-    if (nblk > CSW_NOALLOC_MAX_BLOCKS || nv > CSW_NOALLOC_MAX_VARS)
+    if (!csw_noalloc_fits(nc, nv))
         return csw::solver_fail(s, CSWDG_EINVAL, "conservation_noalloc: %d cells exceed the fixed scratch (at most %d cells)", nc,
-                                CSW_NOALLOC_MAX_BLOCKS * 256);
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: device query failed");
-    if (!g_noalloc_ptr[dev]) {
-        // one-time set-up on this device: the device address of the scratch array
+                                CSW_NOALLOC_MAX_BLOCKS * CSW_NOALLOC_CELLS_PER_BLOCK);
+    if (dev < 0 || dev >= kMaxDevices) return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: solver device %d", dev);
+    // the solver's device is current for the look-up and the launches (its stream belongs to it)
+    DeviceGuard guard(dev);
+    if (guard.err != cudaSuccess)
+        return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: cudaSetDevice(%d): %s", dev, cudaGetErrorString(guard.err));
+    std::call_once(g_noalloc_once[dev], [dev] {
         double *ptr = nullptr;
-        e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_partial);
-        if (e != cudaSuccess || !ptr)
-            return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_err[dev] = cudaGetSymbolAddress((void **)&ptr, g_noalloc_partial);
         g_noalloc_ptr[dev] = ptr;
-    }
+    });
+    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev])
+        return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(g_noalloc_err[dev]));
     if (fp32)
         csw::launch_conservation<float>(nc, ld, nv, np, area, (const float *)modes_dev, g_noalloc_ptr[dev], sums_dev, st);
     else
         csw::launch_conservation<double>(nc, ld, nv, np, area, (const double *)modes_dev, g_noalloc_ptr[dev], sums_dev, st);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: %s", cudaGetErrorString(e));
     return CSWDG_OK;
 }
-

@@ -4,11 +4,12 @@
   whole run against the oracle (coefficients 1e-11, flags bit-exact at the end).
 * Burgers P2, 160x160 (51,200 cells): 12 steps against the oracle in FP64
   (1e-11, flags) and in FP32-bulk mode (L1 error relative to the mean |u|
-  below 2e-6); then the GPU alone to t = 0.3 (about 1,900 steps; KXRCF starts
-  flagging cells near t = 0.22): cell-mean conservation, limited cells present,
-  maximum principle, FP32 vs FP64 L1 difference.  On this 51,200-cell mesh the
-  run does not reach t = 1.0: from t ~ 0.45 the repeatedly reconstructed
-  flagged cells grow without bound in both precisions (see the design notes).
+  below 2e-6); then the GPU alone through shock formation (t = 2/pi) to the
+  configuration's t = 1.0 in both precisions: cell-mean conservation, limited
+  cells present, cell means within the exact solution's range [0.25, 0.75]
+  up to a stated excursion, and the FP32-bulk L1 difference from FP64 there.
+* Burgers P2, 20x20, through the shock to t = 1.0: the whole run against the
+  oracle in FP64.
 * Double Mach reflection, Euler P2, 960x240 (460,800 cells): one operator
   evaluation and one limiter pass on a seeded random state, compared with the
   oracle on 600 sampled cells (FP64: 1e-11 and identical flags).
@@ -74,26 +75,67 @@ def test_config2_steps_vs_oracle(csw, cuda_stream, precision):
         assert err < 2e-6, err
 
 
-def test_config2_long_run_fp32_vs_fp64(csw, cuda_stream):
+def test_config2_to_t1_fp32_vs_fp64(csw, cuda_stream):
+    """Config 2 to its end time: the shock forms at t = 2/pi and the limiter
+    holds every cell mean within [0.25, 0.75] up to the excursion stated in the
+    bound (the oracle's on 20x20 / 40x40 / 80x80: 7e-4 / 2e-5 / 1.2e-3); checked
+    at 10 times through the run.  The FP32-bulk run is compared with the FP64
+    run (which the 12-step test ties to the oracle) by the area-weighted L1
+    difference of the cell means relative to the mean |u| = 0.5."""
     pb = W.burgers_sine(160, seed=2)
-    out = {}
+    area = W.cell_areas(pb.mesh)
+    out, ext = {}, {}
     for prec in (0, 1):
         s = csw.Solver(0, 2, prec, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=cuda_stream)
         s.setup(pb)
         s.project_ic(pb.u0, apply_limiter=1)
         c0 = s.conservation()[0]
-        t = s.step(0.0, 100000, 0.3)
-        assert t == 0.3
+        hi, lo = 0.0, 1.0
+        for tk in np.linspace(0.1, 1.0, 10):
+            t = s.step(0.0, 1000000, float(tk))
+            assert t == float(tk)
+            m = s.read_modes()[:, 0, 0] / np.sqrt(area)
+            assert np.all(np.isfinite(m))
+            hi, lo = max(hi, m.max()), min(lo, m.min())
         # FP32-bulk: the two sides of a face use geometry factors |n~| = 2|e|/|K| rounded
         # separately to float, a drift of about 6e-9 of the total per step
-        assert abs(s.conservation()[0] - c0) < (1e-11 if prec == 0 else 5e-5) * abs(c0)
-        assert s.num_flagged() > 0  # the detector has started to flag cells
+        assert abs(s.conservation()[0] - c0) < (1e-11 if prec == 0 else 2e-4) * abs(c0)
+        assert s.num_flagged() > 0
+        ext[prec] = (hi - 0.75, 0.25 - lo)
+        assert hi < 0.75 + 3e-3 and lo > 0.25 - 3e-3, ext
         out[prec] = s.read_modes()
-        means = out[prec][:, 0, 0] / np.sqrt(W.cell_areas(pb.mesh))
-        assert means.min() > 0.25 - 1e-3 and means.max() < 0.75 + 1e-3
         s.close()
-    area = W.cell_areas(pb.mesh)
-    assert l1(out[1], out[0], area) < 1e-4
+    err = l1(out[1], out[0], area) / 0.5
+    print(f"config 2 at t = 1: excursions FP64 {ext[0]}, FP32-bulk {ext[1]}; FP32-bulk vs FP64 L1 {err:.3e}")
+    assert err < 1e-3, err
+
+
+def test_burgers_p2_through_the_shock_vs_oracle(csw, cuda_stream):
+    """Burgers P2 on 20x20 to t = 1.0 (the shock forms at 2/pi), whole run in
+    FP64 against the oracle: at the end the flags match and the coefficients
+    agree within 1e-9 of the largest (a shock run amplifies rounding-order
+    differences through the nonlinear weights; single passes are held to
+    1e-11)."""
+    pb = W.burgers_sine(20, seed=2)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    uo = o.limit(o.project(pb.u0), 0.0)[0]
+    s = csw.Solver(0, 2, csw.FP64, csw.LIMITER_KXRCF, c_k=1.0, cfl=0.1, stream=cuda_stream)
+    s.setup(pb)
+    s.write_modes(uo)
+    s.set_time(0.0)
+    t, n, flo = 0.0, 0, None
+    while t < 1.0:
+        dt = min(o.cfl_dt(uo, 0.1), 1.0 - t)
+        uo, flo, st = o.step(uo, t, dt)
+        t += dt
+        n += 1
+    assert abs(s.step(0.0, n + 5, 1.0) - 1.0) < 1e-15
+    ug = s.read_modes()
+    err = np.abs(ug - uo).max() / np.abs(uo).max()
+    nflip = int(np.sum(s.read_flags() != flo))
+    print(f"20x20 P2 to t = 1: {n} steps, max relative coefficient difference {err:.3e}, flags differing {nflip}")
+    assert nflip == 0 and flo.sum() > 0
+    assert err < 1e-9, err
 
 
 def test_config3_full_size_sampled_fp64(csw, cuda_stream):

@@ -19,11 +19,19 @@ def internal_state(torch, s, modes, areas, dtype):
     return torch.tensor(host.ravel(), dtype=dtype, device="cuda").contiguous()
 
 
-@pytest.mark.parametrize("precision,rtol", [(0, 1e-13), (1, 1e-6)])
-def test_conservation_noalloc_matches_allocating_entry_point(csw, cuda_stream, precision, rtol):
+@pytest.mark.parametrize("mesh,precision,rtol", [
+    ("small", 0, 1e-13), ("small", 1, 1e-6), ("small", 2, 1e-6),
+    ("dmr", 0, 1e-13), ("dmr", 1, 1e-6)])
+def test_conservation_noalloc_matches_allocating_entry_point(csw, cuda_stream, mesh, precision, rtol):
+    """small: 338 cells, two reduction blocks with a ragged tail; dmr: the
+    460,800-cell double-Mach mesh, 1,800 blocks.  Precision modes 0 (FP64),
+    1 (FP32 state, FP64 weights) and 2 (FP32 throughout)."""
     import torch
 
-    pb = W.euler_entropy_wave(13, seed=41)  # 338 cells: two reduction blocks, ragged tail
+    if mesh == "small":
+        pb = W.euler_entropy_wave(13, seed=41)
+    else:
+        pb = W.double_mach(960, 240, seed=3)
     s = csw.Solver(csw.EULER, 2, precision, csw.LIMITER_OFF, stream=cuda_stream)
     s.setup(pb)
     areas = W.cell_areas(pb.mesh)
