@@ -81,7 +81,9 @@ def test_config2_to_t1_fp32_vs_fp64(csw, cuda_stream):
     bound (the oracle's on 20x20 / 40x40 / 80x80: 7e-4 / 2e-5 / 1.2e-3); checked
     at 10 times through the run.  The FP32-bulk run is compared with the FP64
     run (which the 12-step test ties to the oracle) by the area-weighted L1
-    difference of the cell means relative to the mean |u| = 0.5."""
+    difference of the cell means relative to the mean |u| = 0.5.  Measured on
+    the GB300: excursions above / below the range 5.4e-4 / 9.8e-4 (FP64) and
+    2.2e-3 / 1.6e-3 (FP32-bulk); FP32-bulk against FP64 L1 1.7e-4."""
     pb = W.burgers_sine(160, seed=2)
     area = W.cell_areas(pb.mesh)
     out, ext = {}, {}
@@ -113,9 +115,8 @@ def test_config2_to_t1_fp32_vs_fp64(csw, cuda_stream):
 def test_burgers_p2_through_the_shock_vs_oracle(csw, cuda_stream):
     """Burgers P2 on 20x20 to t = 1.0 (the shock forms at 2/pi), whole run in
     FP64 against the oracle: at the end the flags match and the coefficients
-    agree within 1e-9 of the largest (a shock run amplifies rounding-order
-    differences through the nonlinear weights; single passes are held to
-    1e-11)."""
+    agree within 1e-11 of the largest (measured on the GB300: 708 steps,
+    2.6e-14, no flag differs)."""
     pb = W.burgers_sine(20, seed=2)
     o = oracle.Oracle(pb, k=2, limiter=1)
     uo = o.limit(o.project(pb.u0), 0.0)[0]
@@ -135,7 +136,7 @@ def test_burgers_p2_through_the_shock_vs_oracle(csw, cuda_stream):
     nflip = int(np.sum(s.read_flags() != flo))
     print(f"20x20 P2 to t = 1: {n} steps, max relative coefficient difference {err:.3e}, flags differing {nflip}")
     assert nflip == 0 and flo.sum() > 0
-    assert err < 1e-9, err
+    assert err < 1e-11, err
 
 
 def test_config3_full_size_sampled_fp64(csw, cuda_stream):
