@@ -101,6 +101,14 @@ def stage_bytes_per_cell(fp32: bool) -> float:
     return (3 * (2 * S + geo + kx) + 2 * S) / 3.0
 
 
+# FP64 flops of the Euler P2 operator + RK stage per cell (FMA = 2, reciprocal and
+# square root = 1), counted from the stage kernel: 7 volume points x 147 (trace
+# 40, flux 19, accumulation 88), 12 face points x 199 (two traces 80, local
+# Lax-Friedrichs flux 67, accumulation 52), RK update 120, KXRCF record and the
+# positivity screen 110
+STAGE_FLOPS_PER_CELL_EULER_P2 = 7 * 147 + 12 * 199 + 120 + 110
+
+
 def read_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -337,9 +345,19 @@ def run_ours(args):
         f1.record()
         torch.cuda.synchronize()
         ms2 = f0.elapsed_time(f1)
+        prof2, _ = s2.profile_step(0.0, max(1, min(args.profile_steps, nsteps)), NO_END)
         s2.close()
-        return {"value": float(nc) * NP * NV * 3 * nsteps / (ms2 * 1e-3), "unit": UNIT,
-                "ms_per_step": ms2 / nsteps, "steps": nsteps, "precision": what}
+        out2 = {"value": float(nc) * NP * NV * 3 * nsteps / (ms2 * 1e-3), "unit": UNIT,
+                "ms_per_step": ms2 / nsteps, "steps": nsteps, "precision": what,
+                "kernel_ms_per_step": {k: v / max(1, min(args.profile_steps, nsteps)) for k, v in prof2.items()}}
+        if precision == csw.FP64 and fp64_peak:
+            st_ms = out2["kernel_ms_per_step"]["stage"] / 3.0
+            ach = nc * STAGE_FLOPS_PER_CELL_EULER_P2 / (st_ms * 1e-3) / 1e9
+            out2["roofline_fp64"] = {"bound": "fp64", "kernel": "k_stage (FP64 mode)", "achieved": ach,
+                                     "peak": fp64_peak, "unit": "GFLOP/s", "frac": ach / fp64_peak,
+                                     "flops_per_cell": STAGE_FLOPS_PER_CELL_EULER_P2,
+                                     "peak_source": "measured: cswdg_probe_fp64_fma (FP64 FMA chains, CUDA events)"}
+        return out2
 
     def adjoint(nsteps):
         """Hand-written adjoint on the isentropic-vortex workload (periodic
@@ -393,6 +411,10 @@ def run_ours(args):
         return {"steps": nsteps, "dt": dtl, "quantity": "density cell means", "from_t": t_dev,
                 "l1_rel": float(np.sum(area * np.abs(rho32 - rho64)) / np.sum(area * np.abs(rho64)))}
 
+    try:
+        fp64_peak = csw.probe_fp64_fma(stream)
+    except Exception:
+        fp64_peak = None
     adj = adjoint(args.adjoint_steps)
     fp32 = secondary(csw.FP32, args.fp32_steps, "FP32 mode: smoothness indicators and nonlinear weights in float as well "
                                                  "(quotient forms), FP64 only for close calls of the decisions")
@@ -433,6 +455,7 @@ def run_ours(args):
         "fp32_bulk_vs_fp64_l1": l1_vs_fp64(args.l1_steps),
         "fp32_weights": fp32,
         "fp64": fp64,
+        "fp64_peak_gflops": fp64_peak,
     }
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample, workload=args.workload)

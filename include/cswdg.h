@@ -311,6 +311,15 @@ cswdg_status cswdg_stencil_operator(cswdg_solver *s, int64_t cell, double *out_h
  * needed.  Errors: EINVAL, ECUDA. */
 cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *modes_dev, double *sums_dev);
 
+/* FP64 FMA throughput of the current device, measured (no counterpart in the
+ * paper; the ceiling for the FP64-pipe-bound parts of the path): 5 launches of
+ * 8 x SMs blocks of 256 threads, each thread running 8 independent chains of
+ * 4,096 fused multiply-adds, timed with CUDA events on `stream` (a
+ * cudaStream_t, 0 for the default stream).  *gflops_out receives 2 x FMAs / s
+ * in GFLOP/s.  Allocates one 8-byte device word for the duration of the call.
+ * Errors: EINVAL (null output), ENOMEM, ECUDA. */
+cswdg_status cswdg_probe_fp64_fma(void *stream, double *gflops_out);
+
 /* Host-side mesh processing alone, without a solver or a device (no
  * counterpart in the paper; for tests and inspection): the connectivity,
  * periodic pairing, locality order and geometry that cswdg_mesh_upload builds.

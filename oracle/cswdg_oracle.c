@@ -746,6 +746,34 @@ static double circumradius(const Tri *t)
     return a * b * c / (4.0 * tri_area(t));
 }
 
+/* Reading R-pos (the paper states no positivity treatment): 1 if the Euler
+ * polynomial with modes m[v*np + i] on cell c has a non-positive density or
+ * pressure at one of the volume-rule points or the face Gauss points. */
+static int nonphysical_points(const Oracle *o, int c, const double *m)
+{
+    int np = o->np;
+    Tri tc = cell_tri(o, c, 0, 0);
+    for (int q = 0; q < o->vol.n + 3 * o->nfq; ++q) {
+        double x, y, U[4] = {0.0, 0.0, 0.0, 0.0};
+        if (q < o->vol.n) {
+            tri_point(&tc, o->vol.b[q], &x, &y);
+        } else {
+            int f = (q - o->vol.n) / o->nfq, g = (q - o->vol.n) % o->nfq;
+            double ax, ay, bx, by, nx, ny, len;
+            face_geom(o, c, f, &ax, &ay, &bx, &by, &nx, &ny, &len);
+            x = ax + o->fx[g] * (bx - ax);
+            y = ay + o->fx[g] * (by - ay);
+        }
+        for (int i = 0; i < np; ++i) {
+            double pm;
+            psi_phys(o, &tc, i, x, y, &pm, NULL, NULL);
+            for (int v = 0; v < 4; ++v) U[v] += m[v * np + i] * pm;
+        }
+        if (!(U[0] > 0.0 && euler_p(o->gam, U) > 0.0)) return 1;
+    }
+    return 0;
+}
+
 static int detect_cell(const Oracle *o, const double *u, double t, int c, double *Rout)
 {
     int nv = o->nvar, np = o->np;
@@ -786,6 +814,10 @@ static int detect_cell(const Oracle *o, const double *u, double t, int c, double
     else if (nrm == 0.0) R = (fabs(jump) > 0.0) ? INFINITY : 0.0;
     else R = fabs(jump) / (hp * inlen * nrm);
     if (Rout) *Rout = R;
+    /* Reading R-pos: a cell whose polynomial is non-physical at a quadrature
+     * point is troubled whatever its indicator (the operator would take the
+     * sound speed of a non-positive pressure there) */
+    if (o->eq == EQ_EULER && nonphysical_points(o, c, u + (size_t)c * nv * np)) return 1;
     return R > o->ck;
 }
 
@@ -1265,31 +1297,9 @@ static int limit_cell(const Oracle *o, const double *u, double t, int c, double 
      * reconstructed polynomial has a non-positive density or pressure at a
      * volume-rule point or a face Gauss point of the cell, the cell keeps
      * only its mean. */
-    {
-        Tri tc = cell_tri(o, c, 0, 0);
-        int bad = 0;
-        for (int q = 0; q < o->vol.n + 3 * o->nfq && !bad; ++q) {
-            double x, y, U[4] = {0.0, 0.0, 0.0, 0.0};
-            if (q < o->vol.n) {
-                tri_point(&tc, o->vol.b[q], &x, &y);
-            } else {
-                int f = (q - o->vol.n) / o->nfq, g = (q - o->vol.n) % o->nfq;
-                double ax, ay, bx, by, nx, ny, len;
-                face_geom(o, c, f, &ax, &ay, &bx, &by, &nx, &ny, &len);
-                x = ax + o->fx[g] * (bx - ax);
-                y = ay + o->fx[g] * (by - ay);
-            }
-            for (int m = 0; m < np; ++m) {
-                double pm;
-                psi_phys(o, &tc, m, x, y, &pm, NULL, NULL);
-                for (int v = 0; v < 4; ++v) U[v] += out[v * np + m] * pm;
-            }
-            if (!(U[0] > 0.0 && euler_p(o->gam, U) > 0.0)) bad = 1;
-        }
-        if (bad)
-            for (int v = 0; v < 4; ++v)
-                for (int i = 1; i < np; ++i) out[v * np + i] = 0.0;
-    }
+    if (nonphysical_points(o, c, out))
+        for (int v = 0; v < 4; ++v)
+            for (int i = 1; i < np; ++i) out[v * np + i] = 0.0;
     return status;
 }
 

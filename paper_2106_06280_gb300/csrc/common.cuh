@@ -99,6 +99,7 @@ template <typename R, int K> struct Tab {
     R fint[3][Deg<K>::NP];            // sum_g fw[g] psi_m(point g of face f): the face mean of psi_m
     R vdrw[Deg<K>::QV][Deg<K>::NP];   // vw[q] d psi_m / dr (weight folded in, rounded once)
     R vdsw[Deg<K>::QV][Deg<K>::NP];   // vw[q] d psi_m / ds
+    R pmax[Deg<K>::NP];               // max of |psi_m| over the volume and face points (rounded up)
 };
 
 // Traces seen from the neighbour: psi_m at the Gauss points of local face nf

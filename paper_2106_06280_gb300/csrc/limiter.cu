@@ -448,6 +448,12 @@ __device__ __forceinline__ int detect_cell(const MeshDev<R> &M, const R *__restr
         if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
     }
     if (all) return 1;
+    // reading R-pos: non-physical at a volume or face quadrature point -> troubled
+    if constexpr (EQ == EULER) {
+        R uf[4][NP];
+        load_cell<4, NP>(u, c, uf);
+        if (nonphys_points<K, R>(uf, T, M.gamma)) return 1;
+    }
     R num = R(0), lsum = R(0);
     const unsigned nbfc = M.nbf[c];
 #pragma unroll
@@ -998,6 +1004,8 @@ __device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R (&k8)[KX_STR
 {
     constexpr int QF = Deg<K>::QF;
     const Tab<R, K> &T = ltab<R, K>();
+    // a negative norm marks a polynomial that is non-physical at a quadrature point (R-pos)
+    if (k8[KX_NRM2] < R(0)) return 1;
     R num = R(0), lsum = R(0);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {

@@ -236,6 +236,10 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
             R n2 = R(0);
 #pragma unroll
             for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
+            // reading R-pos: a polynomial that is non-physical at a quadrature point
+            // makes the cell troubled; the detection reads a negative norm as that mark
+            if constexpr (EQ == EULER)
+                if (nonphys_points<K, R>(res, T, M.gamma)) n2 = R(-1);
             k7[KX_NRM2] = n2;
             // the new means: physically admissible (Euler: rho > 0, p > 0; screened
             // in the state precision, close calls in double), and the mean velocity
@@ -587,5 +591,57 @@ extern "C" cswdg_status cswdg_conservation_noalloc(cswdg_solver *s, const void *
         csw::launch_conservation<double>(nc, ld, nv, np, area, (const double *)modes_dev, g_noalloc_ptr[dev], sums_dev, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return csw::solver_fail(s, CSWDG_ECUDA, "conservation_noalloc: %s", cudaGetErrorString(e));
+    return CSWDG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe: the ceiling of the FP64-pipe-bound work (the
+// FP64 mode and the double smoothness-indicator and weight arithmetic of the
+// reconstruction).  Every thread runs 8 independent FMA chains; the grid fills
+// every SM several times over.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_probe_dfma(int iters, double b, double c, double *sink)
+{
+    double a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = 1e-3 * (threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = fma(a[i], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += a[i];
+    if (s == 12345.678) sink[0] = s;  // keeps the chains live; never true for these inputs
+}
+
+extern "C" cswdg_status cswdg_probe_fp64_fma(void *stream, double *gflops_out)
+{
+    if (!gflops_out) return CSWDG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CSWDG_ECUDA;
+    double *sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess) return CSWDG_ENOMEM;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = nsm * 8, threads = 256, iters = 4096;
+    // 1 - 1e-9 and 1e-9 keep every chain finite and away from zero
+    k_probe_dfma<<<blocks, threads, 0, st>>>(iters, 1.0 - 1e-9, 1e-9, sink);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 5; ++r) k_probe_dfma<<<blocks, threads, 0, st>>>(iters, 1.0 - 1e-9, 1e-9, sink);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess || !(ms > 0.f)) return CSWDG_ECUDA;
+    const double flops = 5.0 * blocks * (double)threads * iters * 8 * 2;
+    *gflops_out = flops / (ms * 1e-3) / 1e9;
     return CSWDG_OK;
 }

@@ -147,4 +147,53 @@ __host__ __device__ __forceinline__ void ghost(const BFace &bf, const BcTab *bc,
     }
 }
 
+// Reading R-pos as a detection trigger: 1 if the Euler polynomial with modes
+// U[v][m] (internal scaling, table T) has a non-positive density or pressure at
+// one of the volume points or face Gauss points.  A bound screens first: every
+// point value of variable v lies within sum_{m>=1} |U_vm| max|psi_m| of the
+// mean's share, and rho_lo > 0, E_lo > 0, 2 E_lo rho_lo > |m|_hi^2 imply
+// 2 E rho > |m|^2 (p > 0) at every point; only cells that fail it are checked
+// point by point (state precision with a relative margin, close calls in
+// double), so the outcome is that of the point-by-point check.
+template <int K, typename R>
+__device__ __forceinline__ bool nonphys_points(const R (&U)[4][Deg<K>::NP], const Tab<R, K> &T, double gam)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF;
+    R lo[4], hi[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        R d = R(0);
+#pragma unroll
+        for (int m = 1; m < NP; ++m) d += rabs(U[v][m]) * T.pmax[m];
+        const R c = U[v][0] * T.vphi[0][0];
+        lo[v] = c - d;
+        hi[v] = c + d;
+    }
+    if (lo[0] > R(0) && lo[3] > R(0)) {
+        const R mx = rmax(rabs(lo[1]), rabs(hi[1])), my = rmax(rabs(lo[2]), rabs(hi[2]));
+        if (R(2) * lo[3] * lo[0] > R(1.001) * (mx * mx + my * my)) return false;
+    }
+#pragma unroll 1
+    for (int q = 0; q < QV + 3 * QF; ++q) {
+        const R *phi = (q < QV) ? T.vphi[q] : T.fphi[(q - QV) / QF][(q - QV) % QF];
+        R P[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            R s = R(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) s += U[v][m] * phi[m];
+            P[v] = s;
+        }
+        const R two_e_rho = R(2) * P[3] * P[0], m2 = P[1] * P[1] + P[2] * P[2];
+        const R qp = two_e_rho - m2;
+        bool ok = (P[0] > R(0)) && (qp > R(1e-3) * (rabs(two_e_rho) + m2));
+        if (!ok && P[0] > R(0) && !(qp < -R(1e-3) * (rabs(two_e_rho) + m2))) {
+            const double r = (double)P[0], mxd = (double)P[1], myd = (double)P[2], E = (double)P[3];
+            ok = (gam - 1.0) * (E - 0.5 * (mxd * mxd + myd * myd) / r) > 0.0;
+        }
+        if (!ok) return true;
+    }
+    return false;
+}
+
 }  // namespace csw

@@ -1,6 +1,8 @@
 // tables.cuh -- host construction of the constant-memory tables (basis values
 // and gradients at the volume points, basis values at the face Gauss points).
 #pragma once
+#include <algorithm>
+#include <cmath>
 #include "common.cuh"
 #include "rules.cuh"
 
@@ -63,6 +65,13 @@ template <typename R, int K> inline void make_tab(Tab<R, K> &T)
                 T.fphi[f][g][m] = (R)v;
             }
         }
+    for (int m = 0; m < NP; ++m) {
+        double mx = 0.0;
+        for (int q = 0; q < QV; ++q) mx = std::max(mx, std::fabs((double)T.vphi[q][m]));
+        for (int f = 0; f < 3; ++f)
+            for (int g = 0; g < QF; ++g) mx = std::max(mx, std::fabs((double)T.fphi[f][g][m]));
+        T.pmax[m] = (R)(mx * (1.0 + 1e-5));
+    }
     for (int f = 0; f < 3; ++f)
         for (int m = 0; m < NP; ++m) {
             double acc = 0.0;

@@ -73,6 +73,7 @@ def _load():
         "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp, dp], C.c_int),
         "cswdg_limit_adjoint": ([vp, C.c_double, dp, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
         "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
+        "cswdg_probe_fp64_fma": ([vp, dp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -89,12 +90,21 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
             "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_selftest_timeout",
             "cswdg_autotune", "cswdg_rhs_adjoint", "cswdg_adjoint_steps", "cswdg_limit_adjoint",
-            "cswdg_set_stage_shape", "cswdg_host_mesh"]
+            "cswdg_set_stage_shape", "cswdg_host_mesh", "cswdg_probe_fp64_fma"]
 TUNE_CANDIDATES = 7
 
 
 def _d(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def probe_fp64_fma(stream=None):
+    """Measured FP64 FMA throughput of the current device in GFLOP/s."""
+    g = np.zeros(1)
+    st = lib.cswdg_probe_fp64_fma(C.c_void_p(stream or 0), _p(g))
+    if st != 0:
+        raise CswdgError(st, "cswdg_probe_fp64_fma failed")
+    return float(g[0])
 
 
 def host_mesh(problem, degree):

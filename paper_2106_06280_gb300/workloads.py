@@ -228,8 +228,11 @@ def dmr_states(gamma=GAMMA):
 def double_mach(nx: int = 960, ny: int = 240, seed: int = 3) -> Problem:
     """Sec. 4.2 Example 5: Mach 10 shock through (1/6, 0) at 60 degrees on
     [0,4]x[0,1].  Tags: 1 post-shock inflow (left side and bottom x < 1/6),
-    2 reflecting wall (bottom x >= 1/6), 3 outflow (right), 4 top boundary
-    following the exact shock position x_s(t) = 1/6 + (1 + 20 t)/sqrt(3)."""
+    2 reflecting wall (bottom x >= 1/6), 3 right side: the undisturbed
+    pre-shock state (the exact solution there up to t = 0.28, when the
+    incident shock reaches x = 4; the paper leaves this side to the cited
+    set-up), 4 top boundary following the exact shock position
+    x_s(t) = 1/6 + (1 + 20 t)/sqrt(3)."""
     pre, post = dmr_states()
 
     def tag_fn(side, xm, ym):
@@ -247,7 +250,7 @@ def double_mach(nx: int = 960, ny: int = 240, seed: int = 3) -> Problem:
         post_region = x < DMR_X0 + y * DMR_COT
         return np.where(post_region[:, None], post[None, :], pre[None, :])
 
-    bnd = {1: (DIRICHLET, list(post)), 2: (WALL, []), 3: (TRANSMISSIVE, []),
+    bnd = {1: (DIRICHLET, list(post)), 2: (WALL, []), 3: (DIRICHLET, list(pre)),
            4: (SHOCKLINE, [DMR_X0, DMR_COT, DMR_SPEED] + list(post) + list(pre))}
     return Problem("double_mach", 1, mesh, u0, bnd, 0.2, None)
 

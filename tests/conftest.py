@@ -11,6 +11,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long CPU oracle runs")
+    config.addinivalue_line("markers", "gpu_long: full-size GPU checks of many minutes, run on request (-m gpu_long)")
 
 
 @pytest.fixture(scope="session")

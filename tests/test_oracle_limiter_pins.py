@@ -196,3 +196,46 @@ def test_burgers_shock_stays_in_range_under_refinement(k, bound):
     ex = [max(_shock_run(n, k)) for n in (20, 40)]
     assert max(ex) < bound, ex
     assert ex[1] < ex[0] + 0.1 * bound, ex
+
+
+def test_positivity_trigger_and_fallback():
+    """Reading R-pos.  (a) A uniform gas at rest with one cell given a density
+    slope that makes its polynomial negative at some points: no face is an
+    inflow face, so R = 0, yet the cell is troubled because its polynomial is
+    non-physical at a quadrature point; its neighbours are uniform, so the
+    reconstruction returns the mean alone.  (b) A low-density cell between a
+    near-vacuum neighbour and dense ones: the limited polynomial keeps the
+    mean and is physical at every volume point (evaluated independently here
+    from the modes and the basis' closed form at the points)."""
+    pb = W.euler_entropy_wave(4, seed=12)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    area = W.cell_areas(pb.mesh)
+    base = W.prim_to_cons(np.array([1.0]), 0.0, 0.0, 1.0)[0]
+    u = np.zeros((pb.mesh.nc, 4, 6))
+    u[:, :, 0] = base[None, :] * np.sqrt(area)[:, None]
+    c = 5
+    u1 = u.copy()
+    u1[c, 0, 1] = 2.0 * u1[c, 0, 0]  # a first-mode coefficient twice the mean's: negative near one edge
+    xy = o.volume_points()[c]
+    rho_pts = o.eval_points(u1, np.full(len(xy), c, dtype=np.int32), xy)[:, 0]
+    fl, R = o.detect(u1)
+    assert R[c] == 0.0 and fl[c] == 1 and fl.sum() == 1
+    out, st = o.limit_cell(u1, c)
+    assert st == 0 and out[0, 0] == u1[c, 0, 0]
+    assert np.abs(out[:, 1:]).max() < 1e-14 * np.abs(out[:, 0]).max()
+    nb = o.connectivity()[0]
+    for scale in (1e-3, 1e-2, 0.1):
+        u2 = u.copy()
+        for j, d in enumerate(nb[c]):
+            u2[d, :, 0] = W.prim_to_cons(np.array([[scale, 1.0, 3.0][j]]), 0.0, 0.0, scale)[0] * np.sqrt(area[d])
+        u2[c, :, 0] = W.prim_to_cons(np.array([0.02]), 0.0, 0.0, scale)[0] * np.sqrt(area[c])
+        u2[c, 0, 1:] = 0.5 * u2[c, 0, 0]
+        assert o.detect(u2)[0][c] == 1
+        out2, st = o.limit_cell(u2, c)
+        assert st == 0 and np.array_equal(out2[:, 0], u2[c, :, 0])
+        v = u2.copy()
+        v[c] = out2
+        U = o.eval_points(v, np.full(len(xy), c, dtype=np.int32), xy)
+        p = (W.GAMMA - 1.0) * (U[:, 3] - 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2) / U[:, 0])
+        assert U[:, 0].min() > 0.0 and p.min() > 0.0, scale
+    assert rho_pts.min() < 0.0  # case (a) really starts non-physical at a volume point

@@ -597,10 +597,10 @@ def test_dmr_boundaries_follow_the_exact_shock_position():
     """Sec. 4.2 Example 5 boundaries (reading R-bc) against the closed form of
     the shock position: with the post-shock state everywhere, the operator
     vanishes in every cell whose ghosts equal that state (left and bottom
-    x < 1/6 inflow, right outflow, top boundary left of the Mach-10 front at
+    x < 1/6 inflow, top boundary left of the Mach-10 front at
     x_s(t) = 1/6 + (1 + 20 t)/sqrt(3)) and not in the cells on the top boundary
-    right of the front (pre-shock ghost) nor on the reflecting wall (the
-    post-shock flow crosses it)."""
+    right of the front nor on the right side (pre-shock ghosts) nor on the
+    reflecting wall (the post-shock flow crosses it)."""
     pb = W.double_mach(48, 12, seed=3)
     m = pb.mesh
     post = np.array(pb.boundaries[1][1], dtype=float)
@@ -618,7 +618,7 @@ def test_dmr_boundaries_follow_the_exact_shock_position():
     for v0, v1, tag in m.bface:
         c = cell_of[(min(v0, v1), max(v0, v1))]
         xa, xb = sorted((m.xy[v0, 0], m.xy[v1, 0]))
-        if tag == 2:
+        if tag == 2 or tag == 3:
             kind = 1
         elif tag == 4:
             kind = 0 if xb < xs - 0.1 * h else (1 if xa > xs + 0.1 * h else -1)
