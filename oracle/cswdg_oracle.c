@@ -699,6 +699,11 @@ static void rhs_cell(const Oracle *o, const double *u, double t, int c, double *
             double px = ax + o->fx[g] * (bx - ax), py = ay + o->fx[g] * (by - ay);
             double Uin[4], Uout[4], F[4];
             face_traces(o, u, c, f, px, py, nx, ny, t, Uin, Uout);
+            /* reading R-bc: across a transmissive face the outside state of the flux is
+             * the cell mean (zero-gradient extrapolation of the cell average); the
+             * interior trace itself would leave the flux F(u-) without dissipation */
+            if (o->nb[3 * c + f] < 0 && o->bkind[o->btag[3 * c + f]] == BC_TRANSMISSIVE)
+                for (int v = 0; v < nv; ++v) Uout[v] = u[(size_t)(c * nv + v) * np] / sqrt(area);
             llf_flux(o, Uin, Uout, nx, ny, F);
             for (int i = 0; i < np; ++i) {
                 double p;

@@ -211,6 +211,8 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
                     Uo[v] = s;
                     mu[v] -= T.fw[gr] * snl_nb * sl;
                 }
+            } else if (kind == BC_TRANSMISSIVE) {
+                for (int v = 0; v < NV; ++v) Uo[v] = uc[v][0] * T.vphi[0][0];  // the cell mean (reading R-bc)
             } else {
                 ghost<EQ, R>(bf, M.bc, (double)T.ft[g_], stage_time(ctl, tfac), Ui, Uo);
             }
@@ -223,8 +225,11 @@ __global__ void __launch_bounds__(128) k_rhs_adj(MeshDev<R> M, const R *__restri
                 for (int v = 0; v < NV; ++v) { dUi[v] = gR[v]; dUo[v] = gL[v]; }
             }
             if (code < 0) {
-                // the ghost as a function of the interior trace
-                if (kind == BC_TRANSMISSIVE || kind == BC_PERIODIC) {
+                // the ghost as a function of the interior: the cell mean (transmissive,
+                // mode 0 only) or the trace (wall)
+                if (kind == BC_TRANSMISSIVE) {
+                    for (int v = 0; v < NV; ++v) g[v][0] += T.vphi[0][0] * dUo[v];
+                } else if (kind == BC_PERIODIC) {
                     for (int v = 0; v < NV; ++v) dUi[v] += dUo[v];
                 } else if (kind == BC_WALL) {
                     if (EQ == EULER) {

@@ -196,11 +196,18 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
             }
         } else {
             const BFace bf = M.bf[-code - 1];
+            // a transmissive face takes the cell mean as the outside state (reading R-bc)
+            const bool transmissive = M.bc->kind[bf.tag] == BC_TRANSMISSIVE;
 #pragma unroll
             for (int g = 0; g < QF; ++g) {
                 R Ui[NV], Uo[NV];
                 trace<NV, NP, R>(m0, u, T.fphi[f][g], Ui);
-                ghost<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), Ui, Uo);
+                if (transmissive) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) Uo[v] = m0[v];
+                } else {
+                    ghost<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), Ui, Uo);
+                }
                 face_point<EQ, NV, NP, R>(Ui, Uo, nx, ny, gam, T.fw[g] * hnl, T.fphi[f][g], acc);
             }
         }

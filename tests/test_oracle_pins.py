@@ -136,10 +136,20 @@ def _transmissive_box(n, seed, eq):
     return W.Problem("box", eq, mesh, None, {2: (W.TRANSMISSIVE, [])})
 
 
+def _on_box_side(a, b):
+    """Both end points on one side of the unit square."""
+    return any(a[j] == v and b[j] == v for j in (0, 1) for v in (0.0, 1.0))
+
+
 @pytest.mark.parametrize("k", [1, 2])
 def test_rhs_exact_for_continuous_polynomial_burgers(k):
     """Continuous degree-k data: jumps vanish, every quadrature is exact, so
-    L_h(u) is the L2 projection of -u (u_x + u_y) (integration by parts)."""
+    in a cell without boundary faces L_h(u) is the L2 projection of
+    -u (u_x + u_y) (integration by parts).  A transmissive face takes the cell
+    mean ubar as the flux's outside state (reading R-bc), which adds
+    -int_e psi_i (F*(u-, ubar) - F(u-)).n ds for that face; that term is formed
+    here independently (the method's face rule, numpy's Gauss-Legendre with
+    2 / 4 points, and the local Lax-Friedrichs flux of Burgers written out)."""
     pb = _transmissive_box(4, 3, 0)
     o = oracle.Oracle(pb, k=k, limiter=0)
     if k == 1:
@@ -161,9 +171,31 @@ def test_rhs_exact_for_continuous_polynomial_burgers(k):
         A = np.array([[T[1, 0] - T[0, 0], T[2, 0] - T[0, 0]], [T[1, 1] - T[0, 1], T[2, 1] - T[0, 1]]])
         rs = np.linalg.solve(A, (P - T[0]).T).T * 2 - 1
         g = -f(P[:, 0], P[:, 1]) * (fx(P[:, 0], P[:, 1]) + fy(P[:, 0], P[:, 1]))
+        extra = np.zeros(o.np)
+        ubar = tri_mean(T, f)
+        cen = T.mean(axis=0)
+        for e in range(3):
+            a, b = T[e], T[(e + 1) % 3]
+            if not _on_box_side(a, b):
+                continue
+            d = b - a
+            L_e = np.hypot(*d)
+            n = np.array([d[1], -d[0]]) / L_e
+            if n @ (0.5 * (a + b) - cen) < 0:
+                n = -n
+            xg, wg = np.polynomial.legendre.leggauss(2 if k == 1 else 4)  # the face rule (R-weak): max() is not polynomial
+            Q = a[None, :] + 0.5 * (xg[:, None] + 1.0) * d[None, :]
+            um = f(Q[:, 0], Q[:, 1])
+            sn = n[0] + n[1]
+            alpha = np.maximum(np.abs(um), abs(ubar)) * abs(sn)
+            fstar = 0.5 * (0.5 * um ** 2 + 0.5 * ubar ** 2) * sn - 0.5 * alpha * (ubar - um)
+            rsq = np.linalg.solve(A, (Q - T[0]).T).T * 2 - 1
+            for i in range(o.np):
+                psi_e = np.array([oracle.psi(k, i, r, s)[0] for r, s in rsq]) * math.sqrt(2 / area)
+                extra[i] -= np.sum(0.5 * wg * L_e * psi_e * (fstar - 0.5 * um ** 2 * sn))
         for i in range(o.np):
             psi = np.array([oracle.psi(k, i, r, s)[0] for r, s in rs]) * math.sqrt(2 / area)
-            assert abs(L[c, 0, i] - np.sum(w * g * psi)) < 1e-12
+            assert abs(L[c, 0, i] - np.sum(w * g * psi) - extra[i]) < 1e-12
 
 
 @pytest.mark.parametrize("k", [1, 2])
