@@ -145,7 +145,8 @@ cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st
     if (s->fp32) {
         MeshDev<float> M = mesh_dev<float>(s);
         if (after_stage)
-            launch_detect_kx<float>(s->eq, s->k, M, (const float *)s->kx, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+            launch_detect_kx<float>(s->eq, s->k, M, (const float *)u, (const float *)s->kx, s->ctl, tfac, s->cfg.c_k, all, s->flags,
+                                    s->flist, st);
         else
             launch_detect<float>(s->eq, s->k, M, (const float *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
         mark(prof, KC_DETECT, st);
@@ -157,7 +158,8 @@ cswdg_status limiter_pass(cswdg_solver *s, void *u, double tfac, cudaStream_t st
     } else {
         MeshDev<double> M = mesh_dev<double>(s);
         if (after_stage)
-            launch_detect_kx<double>(s->eq, s->k, M, (const double *)s->kx, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
+            launch_detect_kx<double>(s->eq, s->k, M, (const double *)u, (const double *)s->kx, s->ctl, tfac, s->cfg.c_k, all,
+                                     s->flags, s->flist, st);
         else
             launch_detect<double>(s->eq, s->k, M, (const double *)u, s->ctl, tfac, s->cfg.c_k, all, s->flags, s->flist, st);
         mark(prof, KC_DETECT, st);

@@ -83,8 +83,8 @@ void launch_detect(int eq, int k, const MeshDev<R> &M, const R *u, Ctl *ctl, dou
                    int32_t *flist, cudaStream_t st);
 // KXRCF detection from the precursors the stage kernel wrote (kx)
 template <typename R>
-void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *kx, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
-                      int32_t *flist, cudaStream_t st);
+void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *u, const R *kx, Ctl *ctl, double tfac, double ck, int all,
+                      uint8_t *flags, int32_t *flist, cudaStream_t st);
 // w32: smoothness indicators and nonlinear weights in float (FP32 mode), else double
 template <typename R>
 void launch_limit(int eq, int k, const MeshDev<R> &M, const R *u, const R *ops, const int32_t *flist, const Ctl *ctl,

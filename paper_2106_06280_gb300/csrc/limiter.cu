@@ -999,13 +999,11 @@ template void launch_detect<double>(int, int, const MeshDev<double> &, const dou
 // KXRCF decision of cell c from its precursor record: the jump integral over
 // the inflow faces in face order (Sec. 3.1), compared in product form
 template <int EQ, int K, typename R>
-__device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R (&k8)[KX_STRIDE], R kap, const Ctl *ctl, double tfac, double ck,
-                                       R ck2, int c)
+__device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R *__restrict__ u, const R (&k8)[KX_STRIDE], R kap, const Ctl *ctl,
+                                       double tfac, double ck, R ck2, int c)
 {
     constexpr int QF = Deg<K>::QF;
     const Tab<R, K> &T = ltab<R, K>();
-    // a negative norm marks a polynomial that is non-physical at a quadrature point (R-pos)
-    if (k8[KX_NRM2] < R(0)) return 1;
     R num = R(0), lsum = R(0);
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
@@ -1031,7 +1029,17 @@ __device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R (&k8)[KX_STR
         num += nl * J;
         lsum += nl;
     }
-    const R nrm2 = k8[KX_NRM2];
+    R nrm2 = k8[KX_NRM2];
+    // a negated norm marks a candidate of reading R-pos: the stage kernel's bound did not
+    // show the new polynomial physical at every quadrature point; check the points
+    if (nrm2 < R(0)) {
+        if constexpr (EQ == EULER) {
+            R uf[4][Deg<K>::NP];
+            load_cell<4, Deg<K>::NP>(u, c, uf);
+            if (nonphys_points_exact<K, R>(uf, T, M.gamma)) return 1;
+        }
+        nrm2 = -nrm2;
+    }
     if (!(lsum > R(0))) return 0;
     const R denr = lsum * kap;
     const R lhs = num * num, rhs = ck2 * denr * denr * nrm2;
@@ -1045,8 +1053,8 @@ __device__ __forceinline__ int kx_flag(const MeshDev<R> &M, const R (&k8)[KX_STR
 // records), all records and kappas loaded before the read of the step's active
 // flag; no load depends on another.  Flagged cells are compacted per warp.
 template <int EQ, int K, typename R, int CPT>
-__global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__restrict__ kx, Ctl *ctl, double tfac, double ck, R ck2,
-                                                   int all, uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
+__global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__restrict__ u, const R *__restrict__ kx, Ctl *ctl, double tfac,
+                                                   double ck, R ck2, int all, uint8_t *__restrict__ flags, int32_t *__restrict__ flist)
 {
     const int c0 = blockIdx.x * blockDim.x * CPT + threadIdx.x;
     R k8[CPT][KX_STRIDE] = {}, kap[CPT] = {};
@@ -1064,7 +1072,7 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
         const int c = c0 + i * (int)blockDim.x;
         int flag = 0;
         if (c < M.nc) {
-            flag = all ? 1 : kx_flag<EQ, K, R>(M, k8[i], kap[i], ctl, tfac, ck, ck2, c);
+            flag = all ? 1 : kx_flag<EQ, K, R>(M, u, k8[i], kap[i], ctl, tfac, ck, ck2, c);
             flags[c] = (uint8_t)flag;
         }
         const unsigned mask = __ballot_sync(0xffffffffu, flag);
@@ -1079,23 +1087,23 @@ __global__ void __launch_bounds__(128) k_detect_kx(MeshDev<R> M, const R *__rest
 }
 
 template <typename R>
-void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *kx, Ctl *ctl, double tfac, double ck, int all, uint8_t *flags,
-                      int32_t *flist, cudaStream_t st)
+void launch_detect_kx(int eq, int k, const MeshDev<R> &M, const R *u, const R *kx, Ctl *ctl, double tfac, double ck, int all,
+                      uint8_t *flags, int32_t *flist, cudaStream_t st)
 {
     constexpr int CPT = 1;  // 2 and 4 cells per thread measured slower (fewer warps in flight)
     const int blk = 128, grd = (M.nc + blk * CPT - 1) / (blk * CPT);
     const R ck2 = (R)(ck * ck);
-#define CSW_DK(E, KK) k_detect_kx<E, KK, R, CPT><<<grd, blk, 0, st>>>(M, kx, ctl, tfac, ck, ck2, all, flags, flist)
+#define CSW_DK(E, KK) k_detect_kx<E, KK, R, CPT><<<grd, blk, 0, st>>>(M, u, kx, ctl, tfac, ck, ck2, all, flags, flist)
     if (eq == BURGERS && k == 1) CSW_DK(BURGERS, 1);
     else if (eq == BURGERS && k == 2) CSW_DK(BURGERS, 2);
     else if (eq == EULER && k == 1) CSW_DK(EULER, 1);
     else CSW_DK(EULER, 2);
 #undef CSW_DK
 }
-template void launch_detect_kx<float>(int, int, const MeshDev<float> &, const float *, Ctl *, double, double, int, uint8_t *,
-                                      int32_t *, cudaStream_t);
-template void launch_detect_kx<double>(int, int, const MeshDev<double> &, const double *, Ctl *, double, double, int, uint8_t *,
-                                       int32_t *, cudaStream_t);
+template void launch_detect_kx<float>(int, int, const MeshDev<float> &, const float *, const float *, Ctl *, double, double, int,
+                                      uint8_t *, int32_t *, cudaStream_t);
+template void launch_detect_kx<double>(int, int, const MeshDev<double> &, const double *, const double *, Ctl *, double, double, int,
+                                       uint8_t *, int32_t *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Asynchronous bulk copies global -> shared memory completed on an mbarrier

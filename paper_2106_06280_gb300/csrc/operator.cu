@@ -244,9 +244,12 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
 #pragma unroll
             for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
             // reading R-pos: a polynomial that is non-physical at a quadrature point
-            // makes the cell troubled; the detection reads a negative norm as that mark
+            // makes the cell troubled.  Only the cheap bound runs here (one thread per
+            // cell: the point-by-point check would stall whole warps); a cell that fails
+            // it is handed to the detection as a candidate by a negated norm (n2 > 0
+            // for any cell with a positive mean density)
             if constexpr (EQ == EULER)
-                if (nonphys_points<K, R>(res, T, M.gamma)) n2 = R(-1);
+                if (!physical_by_bound<K, R>(res, T)) n2 = -n2;
             k7[KX_NRM2] = n2;
             // the new means: physically admissible (Euler: rho > 0, p > 0; screened
             // in the state precision, close calls in double), and the mean velocity

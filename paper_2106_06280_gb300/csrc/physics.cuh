@@ -156,9 +156,9 @@ __host__ __device__ __forceinline__ void ghost(const BFace &bf, const BcTab *bc,
 // point by point (state precision with a relative margin, close calls in
 // double), so the outcome is that of the point-by-point check.
 template <int K, typename R>
-__device__ __forceinline__ bool nonphys_points(const R (&U)[4][Deg<K>::NP], const Tab<R, K> &T, double gam)
+__device__ __forceinline__ bool physical_by_bound(const R (&U)[4][Deg<K>::NP], const Tab<R, K> &T)
 {
-    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF;
+    constexpr int NP = Deg<K>::NP;
     R lo[4], hi[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -171,8 +171,16 @@ __device__ __forceinline__ bool nonphys_points(const R (&U)[4][Deg<K>::NP], cons
     }
     if (lo[0] > R(0) && lo[3] > R(0)) {
         const R mx = rmax(rabs(lo[1]), rabs(hi[1])), my = rmax(rabs(lo[2]), rabs(hi[2]));
-        if (R(2) * lo[3] * lo[0] > R(1.001) * (mx * mx + my * my)) return false;
+        if (R(2) * lo[3] * lo[0] > R(1.001) * (mx * mx + my * my)) return true;
     }
+    return false;
+}
+
+// the point-by-point check alone (1: non-physical at some point)
+template <int K, typename R>
+__device__ __forceinline__ bool nonphys_points_exact(const R (&U)[4][Deg<K>::NP], const Tab<R, K> &T, double gam)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF;
 #pragma unroll 1
     for (int q = 0; q < QV + 3 * QF; ++q) {
         const R *phi = (q < QV) ? T.vphi[q] : T.fphi[(q - QV) / QF][(q - QV) % QF];
@@ -194,6 +202,12 @@ __device__ __forceinline__ bool nonphys_points(const R (&U)[4][Deg<K>::NP], cons
         if (!ok) return true;
     }
     return false;
+}
+
+template <int K, typename R>
+__device__ __forceinline__ bool nonphys_points(const R (&U)[4][Deg<K>::NP], const Tab<R, K> &T, double gam)
+{
+    return !physical_by_bound<K, R>(U, T) && nonphys_points_exact<K, R>(U, T, gam);
 }
 
 }  // namespace csw
