@@ -114,8 +114,12 @@ __host__ __device__ inline double dmono(int a, int b, int p, int q, double xi, d
 // Moore-Penrose pseudo-inverse of a full-column-rank m x n matrix (row-major)
 // through Householder QR: P = R^{-1} Q^T, written P[j*m + i].  Returns 0 or -1.
 // Kept out of line: inlined into the set-up kernel, the optimised sm_103a build
-// returned a wrong 9 x 5 pseudo-inverse (the -G build and an out-of-line call
-// agree with the host and with the oracle).
+// (nvcc 13.0, -O3) returns wrong pseudo-inverses for both degrees (the limited
+// modes then differ from the oracle's by 3-12 % relative), while the out-of-line
+// call and the -G build agree with the oracle to 1e-11.  Every array here and in
+// setup_cell covers its largest use (m <= 15 rows, n <= 9 columns, 16-entry
+// scratch, 16-point rules) and every entry is written before it is read; the
+// cause of the difference is not known.
 __host__ __device__ __noinline__ int pinv_qr(int m, int n, double *A, double *P)
 {
     double diag[16], beta[16];
