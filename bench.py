@@ -323,18 +323,23 @@ def run_ours(args):
     traffic = read_traffic(khash, args.workload)
 
     # end to end: pinned host state in, one step, state out, through the C interface
-    host_in = torch.empty((nc, NV, NP), dtype=torch.float64, pin_memory=True).numpy()
-    host_out = torch.empty((nc, NV, NP), dtype=torch.float64, pin_memory=True).numpy()
-    s.read_modes(host_in)
+    # (float host arrays when the state is float: cswdg_write_modes_f32 / read_modes_f32)
+    f32_io = args.precision != "fp64"
+    hdt = torch.float32 if f32_io else torch.float64
+    host_in = torch.empty((nc, NV, NP), dtype=hdt, pin_memory=True).numpy()
+    host_out = torch.empty((nc, NV, NP), dtype=hdt, pin_memory=True).numpy()
+    (s.read_modes_f32 if f32_io else s.read_modes)(host_in)
+    write_fn, read_fn = (s.write_modes_f32, s.read_modes_f32) if f32_io else (s.write_modes, s.read_modes)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        s.write_modes(host_in)
+        write_fn(host_in)
         s.step(0.0, 1, NO_END)
-        s.read_modes(host_out)
+        read_fn(host_out)
     t1 = time.perf_counter()
     e2e_value = float(nc) * NP * NV * 3 * e2e_steps * ws / (t1 - t0)
+    e2e_bytes = nc * NV * NP * (4 if f32_io else 8)
 
     launches = s.launches_per_step(True) * args.steps
     s.close()
@@ -454,9 +459,10 @@ def run_ours(args):
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_cell_algorithmic": bpc, "stage_ms": stage_ms,
                      "kernel_ms_per_step": {k: v / args.profile_steps for k, v in prof.items()}},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nc * NV * NP * 8,
-                "d2h_bytes_per_step": nc * NV * NP * 8, "steps": e2e_steps,
-                "path": "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
+                "d2h_bytes_per_step": e2e_bytes, "steps": e2e_steps,
+                "path": ("cswdg_write_modes_f32(pinned host) + cswdg_step + cswdg_read_modes_f32(pinned host)" if f32_io else
+                         "cswdg_write_modes(pinned host) + cswdg_step + cswdg_read_modes(pinned host)")},
         "gpu_launches": launches,
         "clocks": clk,
         "adjoint": adj,

@@ -236,6 +236,15 @@ cswdg_status cswdg_set_time(cswdg_solver *s, double t);
 cswdg_status cswdg_read_modes(cswdg_solver *s, double *modes_host);
 cswdg_status cswdg_write_modes(cswdg_solver *s, const double *modes_host);
 
+/* cswdg_read_modes / cswdg_write_modes with single-precision host arrays (same
+ * layout: modes_host[(c*nvar + v)*np + m], physically orthonormal basis, user
+ * cell order; caller-owned, nc*nvar*np floats).  In the FP32 and FP32-bulk modes
+ * the state itself is float, so only the basis scaling is rounded to float on
+ * the way; half the bytes of the double pair cross the bus.  Both wait for
+ * their copy.  Errors: EINVAL, ECUDA. */
+cswdg_status cswdg_read_modes_f32(cswdg_solver *s, float *modes_host);
+cswdg_status cswdg_write_modes_f32(cswdg_solver *s, const float *modes_host);
+
 /* Troubled-cell flags of the last limiter pass (1 byte per cell, 0 or 1);
  * with the limiter off all zero. */
 cswdg_status cswdg_read_flags(cswdg_solver *s, uint8_t *flags_host);

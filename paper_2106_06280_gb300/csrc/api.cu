@@ -707,6 +707,33 @@ cswdg_status cswdg_write_modes(cswdg_solver *s, const double *modes)
     return CSWDG_OK;
 }
 
+cswdg_status cswdg_read_modes_f32(cswdg_solver *s, float *modes)
+{
+    if (!s || !s->mesh_ready || !modes) return fail(s, CSWDG_EINVAL, "read_modes_f32");
+    const size_t n = (size_t)s->nc * s->nv * s->np;
+    float *stage = reinterpret_cast<float *>(s->dev_user);  // n floats fit the n-double staging buffer
+    if (s->fp32) launch_to_user<float, float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const float *)s->U, stage, s->stream);
+    else launch_to_user<double, float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, (const double *)s->U, stage, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(modes, stage, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
+cswdg_status cswdg_write_modes_f32(cswdg_solver *s, const float *modes)
+{
+    if (!s || !s->mesh_ready || !modes) return fail(s, CSWDG_EINVAL, "write_modes_f32");
+    const size_t n = (size_t)s->nc * s->nv * s->np;
+    float *stage = reinterpret_cast<float *>(s->dev_user);
+    CK(cudaMemcpyAsync(stage, modes, n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    if (s->fp32) launch_from_user<float, float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, stage, (float *)s->U, s->stream);
+    else launch_from_user<double, float>(s->nc, s->ldc, s->nv, s->np, s->dperm, s->sc, stage, (double *)s->U, s->stream);
+    CK(cudaGetLastError());
+    s->lam_stale = true;
+    CK(cudaStreamSynchronize(s->stream));
+    return CSWDG_OK;
+}
+
 cswdg_status cswdg_read_flags(cswdg_solver *s, uint8_t *flags)
 {
     if (!s || !s->mesh_ready || !flags) return fail(s, CSWDG_EINVAL, "read_flags");

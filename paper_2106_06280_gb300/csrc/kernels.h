@@ -43,10 +43,10 @@ void launch_set_step_params(Ctl *ctl, double dt_fixed, double cfl, double t_end,
 // completes; sets ERR_TIMEOUT
 void launch_selftest_timeout(Ctl *ctl, int polls, cudaStream_t st);
 template <typename R> void launch_project(int k, int nc, int ld, int nv, const double *vals, R *u, cudaStream_t st);
-template <typename R>
-void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st);
-template <typename R>
-void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, double *user, cudaStream_t st);
+template <typename R, typename U>
+void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const U *user, R *u, cudaStream_t st);
+template <typename R, typename U>
+void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, U *user, cudaStream_t st);
 void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st);
 template <typename R>
 void launch_conservation(int nc, int ld, int nv, int np, const double *area, const R *u, double *part, double *out, cudaStream_t st);

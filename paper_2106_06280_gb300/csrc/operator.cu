@@ -441,9 +441,9 @@ template void launch_project<double>(int, int, int, int, const double *, double 
 // Layout conversions.  user[(uc*nv + v)*np + m] (double, physical basis) <->
 // internal [(c*nv + v)*np + m], scaled by sc[c] = sqrt(2/|K|); perm[c] = user index.
 // ---------------------------------------------------------------------------
-template <typename R>
+template <typename R, typename U>
 __global__ void __launch_bounds__(256) k_from_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm,
-                                                   const double *__restrict__ sc, const double *__restrict__ user, R *__restrict__ u)
+                                                   const double *__restrict__ sc, const U *__restrict__ user, R *__restrict__ u)
 {
     // one thread per coefficient: a warp covers consecutive coefficients of one
     // or two cells, so the reads of the cell's user row and the writes of its
@@ -452,19 +452,19 @@ __global__ void __launch_bounds__(256) k_from_user(int nc, int ld, int nv, int n
     const size_t n = (size_t)nc * npv;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / npv), j = (int)(e - (size_t)c * npv);
-        u[e] = (R)(sc[c] * user[(size_t)perm[c] * npv + j]);
+        u[e] = (R)(sc[c] * (double)user[(size_t)perm[c] * npv + j]);
     }
 }
 
-template <typename R>
+template <typename R, typename U>
 __global__ void __launch_bounds__(256) k_to_user(int nc, int ld, int nv, int np, const int32_t *__restrict__ perm,
-                                                 const double *__restrict__ sc, const R *__restrict__ u, double *__restrict__ user)
+                                                 const double *__restrict__ sc, const R *__restrict__ u, U *__restrict__ user)
 {
     const int npv = nv * np;
     const size_t n = (size_t)nc * npv;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
         const int c = (int)(e / npv), j = (int)(e - (size_t)c * npv);
-        user[(size_t)perm[c] * npv + j] = (1.0 / sc[c]) * (double)u[e];
+        user[(size_t)perm[c] * npv + j] = (U)((1.0 / sc[c]) * (double)u[e]);
     }
 }
 
@@ -474,24 +474,28 @@ __global__ void k_flags_to_user(int nc, const int32_t *__restrict__ perm, const 
     if (c < nc) out[perm[c]] = fl[c];
 }
 
-template <typename R>
-void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const double *user, R *u, cudaStream_t st)
+template <typename R, typename U>
+void launch_from_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const U *user, R *u, cudaStream_t st)
 {
     const size_t n = (size_t)nc * nv * np;
     const int grd = (int)std::min<size_t>((n + 255) / 256, 16384);
-    k_from_user<R><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, user, u);
+    k_from_user<R, U><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, user, u);
 }
-template <typename R>
-void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, double *user, cudaStream_t st)
+template <typename R, typename U>
+void launch_to_user(int nc, int ld, int nv, int np, const int32_t *perm, const double *sc, const R *u, U *user, cudaStream_t st)
 {
     const size_t n = (size_t)nc * nv * np;
     const int grd = (int)std::min<size_t>((n + 255) / 256, 16384);
-    k_to_user<R><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, u, user);
+    k_to_user<R, U><<<grd, 256, 0, st>>>(nc, ld, nv, np, perm, sc, u, user);
 }
-template void launch_from_user<float>(int, int, int, int, const int32_t *, const double *, const double *, float *, cudaStream_t);
-template void launch_from_user<double>(int, int, int, int, const int32_t *, const double *, const double *, double *, cudaStream_t);
-template void launch_to_user<float>(int, int, int, int, const int32_t *, const double *, const float *, double *, cudaStream_t);
-template void launch_to_user<double>(int, int, int, int, const int32_t *, const double *, const double *, double *, cudaStream_t);
+#define CSW_UL(R, U)                                                                                                         \
+    template void launch_from_user<R, U>(int, int, int, int, const int32_t *, const double *, const U *, R *, cudaStream_t); \
+    template void launch_to_user<R, U>(int, int, int, int, const int32_t *, const double *, const R *, U *, cudaStream_t);
+CSW_UL(float, double)
+CSW_UL(double, double)
+CSW_UL(float, float)
+CSW_UL(double, float)
+#undef CSW_UL
 
 void launch_flags_to_user(int nc, const int32_t *perm, const uint8_t *fl, uint8_t *out, cudaStream_t st)
 {

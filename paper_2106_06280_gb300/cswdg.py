@@ -74,6 +74,8 @@ def _load():
         "cswdg_limit_adjoint": ([vp, C.c_double, dp, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
         "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
         "cswdg_probe_fp64_fma": ([vp, dp], C.c_int),
+        "cswdg_read_modes_f32": ([vp, C.POINTER(C.c_float)], C.c_int),
+        "cswdg_write_modes_f32": ([vp, C.POINTER(C.c_float)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -90,7 +92,8 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_conservation", "cswdg_eval_rhs", "cswdg_limit", "cswdg_cfl_dt", "cswdg_stage_dev",
             "cswdg_internal_layout", "cswdg_stencil_operator", "cswdg_conservation_noalloc", "cswdg_selftest_timeout",
             "cswdg_autotune", "cswdg_rhs_adjoint", "cswdg_adjoint_steps", "cswdg_limit_adjoint",
-            "cswdg_set_stage_shape", "cswdg_host_mesh", "cswdg_probe_fp64_fma"]
+            "cswdg_set_stage_shape", "cswdg_host_mesh", "cswdg_probe_fp64_fma",
+            "cswdg_read_modes_f32", "cswdg_write_modes_f32"]
 TUNE_CANDIDATES = 7
 
 
@@ -243,6 +246,18 @@ class Solver:
     def write_modes(self, modes):
         modes = _d(modes)
         self._chk(lib.cswdg_write_modes(self.h, _p(modes)))
+
+    def read_modes_f32(self, out=None):
+        """The modal state as float32 (same layout as read_modes)."""
+        if out is None:
+            out = np.zeros((self.nc, self.nvar, self.np), dtype=np.float32)
+        assert out.dtype == np.float32 and out.flags.c_contiguous
+        self._chk(lib.cswdg_read_modes_f32(self.h, _p(out, C.c_float)))
+        return out
+
+    def write_modes_f32(self, modes):
+        modes = np.ascontiguousarray(modes, dtype=np.float32)
+        self._chk(lib.cswdg_write_modes_f32(self.h, _p(modes, C.c_float)))
 
     def read_flags(self):
         f = np.zeros(self.nc, dtype=np.uint8)

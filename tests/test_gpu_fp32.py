@@ -149,3 +149,22 @@ def test_fp32_bulk_vs_fp64_l1_after_20_steps(csw, cuda_stream, dmr):
     r64, r32 = out[csw.FP64], out[csw.FP32_BULK]
     l1 = np.sum(area * np.abs(r32 - r64)) / np.sum(area * np.abs(r64))
     assert l1 < 2e-5, l1
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_float_user_layout_pair(csw, cuda_stream, precision):
+    """cswdg_read_modes_f32 / write_modes_f32 carry the same state as the double
+    pair, to float rounding (each value rounded once to float on the way)."""
+    pb = W.double_mach(24, 6, seed=3)
+    s = csw.Solver(csw.EULER, 2, precision, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    u = W.random_modes(pb.mesh, 4, 6, 61)
+    s.write_modes(u)
+    ud = s.read_modes()
+    uf = s.read_modes_f32()
+    assert uf.dtype == np.float32
+    assert np.abs(uf - ud).max() <= 2e-7 * np.abs(ud).max()
+    s.write_modes_f32(uf)
+    back = s.read_modes()
+    assert np.abs(back - uf.astype(np.float64)).max() <= 2e-7 * np.abs(ud).max()
+    s.close()
