@@ -82,6 +82,7 @@ def lib():
         L.or_hook_frame.argtypes = [vp, C.c_int, _dp]
         L.or_hook_flux.argtypes = [vp, _dp, _dp, C.c_double, C.c_double, _dp]
         L.or_hook_limit_cell.argtypes = [vp, _dp, C.c_double, C.c_int, _dp]
+        L.or_hook_limit_cell_linear.argtypes = [vp, _dp, C.c_double, C.c_int, _dp]
         L.or_euler_eigen.argtypes = [C.c_double, _dp, C.c_double, C.c_double, _dp, _dp]
         _lib = L
     return _lib
@@ -282,6 +283,12 @@ class Oracle:
     def limit_cell(self, u, c, t=0.0):
         out = np.zeros(self.nvar * self.np)
         st = lib().or_hook_limit_cell(self.h, _f64(u), t, c, out)
+        return out.reshape(self.nvar, self.np), st
+
+    def limit_cell_linear(self, u, c, t=0.0):
+        """limit_cell with the linear weights (omega = gamma) in every field."""
+        out = np.zeros(self.nvar * self.np)
+        st = lib().or_hook_limit_cell_linear(self.h, _f64(u), t, c, out)
         return out.reshape(self.nvar, self.np), st
 
 

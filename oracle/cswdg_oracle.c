@@ -1240,7 +1240,7 @@ void or_euler_eigen(double gam, const double *U, double nx, double ny, double *R
 
 /* Limit cell c: reads the unlimited state u, writes the new modes of c into out
  * (nvar*np values; mode 0 of every variable is kept, Sec. 3.2). */
-static int limit_cell(const Oracle *o, const double *u, double t, int c, double *out)
+static int limit_cell_w(const Oracle *o, const double *u, double t, int c, double *out, int force_linear)
 {
     int nv = o->nvar, np = o->np, k = o->k;
     Stencil S;
@@ -1265,7 +1265,7 @@ static int limit_cell(const Oracle *o, const double *u, double t, int c, double 
             for (int i = 0; i < 4; ++i) h1[f][i] = (k == 2) ? hf[f][i][0] : 0.0;
         }
         WenoOut W;
-        weno_scalar(o, &F, &S, ub[0], t1, h1, 0, &W);
+        weno_scalar(o, &F, &S, ub[0], t1, h1, force_linear, &W);
         for (int i = 1; i < np; ++i) out[i] = W.modes[i];
         return W.status;
     }
@@ -1285,7 +1285,7 @@ static int limit_cell(const Oracle *o, const double *u, double t, int c, double 
                 for (int i = 0; i < 4; ++i) { h1[f][i] = 0.0; if (k == 2) for (int j = 0; j < 4; ++j) h1[f][i] += L[fld * 4 + j] * hf[f][i][j]; }
             }
             WenoOut W;
-            weno_scalar(o, &F, &S, w0, t1, h1, 0, &W);
+            weno_scalar(o, &F, &S, w0, t1, h1, force_linear, &W);
             if (W.status) status = W.status;
             for (int i = 1; i < np; ++i) wmodes[fld][i] = W.modes[i];
         }
@@ -1306,6 +1306,11 @@ static int limit_cell(const Oracle *o, const double *u, double t, int c, double 
         for (int v = 0; v < 4; ++v)
             for (int i = 1; i < np; ++i) out[v * np + i] = 0.0;
     return status;
+}
+
+static int limit_cell(const Oracle *o, const double *u, double t, int c, double *out)
+{
+    return limit_cell_w(o, u, t, c, out, 0);
 }
 
 /* Limiter pass: flags (LIM_KXRCF: detected here; LIM_ALL: every cell), then
@@ -1610,3 +1615,5 @@ void or_hook_frame(const Oracle *o, int c, double *out)
 void or_hook_flux(const Oracle *o, const double *UL, const double *UR, double nx, double ny, double *F) { llf_flux(o, UL, UR, nx, ny, F); }
 
 int or_hook_limit_cell(const Oracle *o, const double *u, double t, int c, double *out) { return limit_cell(o, u, t, c, out); }
+/* the same with the linear weights in every field (omega = gamma) */
+int or_hook_limit_cell_linear(const Oracle *o, const double *u, double t, int c, double *out) { return limit_cell_w(o, u, t, c, out, 1); }

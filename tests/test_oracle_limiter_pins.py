@@ -239,3 +239,75 @@ def test_positivity_trigger_and_fallback():
         p = (W.GAMMA - 1.0) * (U[:, 3] - 0.5 * (U[:, 1] ** 2 + U[:, 2] ** 2) / U[:, 0])
         assert U[:, 0].min() > 0.0 and p.min() > 0.0, scale
     assert rho_pts.min() < 0.0  # case (a) really starts non-physical at a volume point
+
+
+def test_euler_characteristic_fields_isolate_the_entropy_wave():
+    """SURVEY C12 / Sec. 3.2 last paragraph (reading R-char), field isolation:
+    entropy-wave data (only the density varies; u = 0.7, v = 0.3, p = 1) lie
+    along the entropy eigenvector (1, u, v, |v|^2/2), which is the same for the
+    x and y directions, so in both characteristic decompositions one field
+    carries the density variation and the other three are constant.  The
+    limited cell must keep its velocity and pressure (momentum and energy modes
+    = u, v and |v|^2/2 times the density modes) and its density modes must be
+    the scalar reconstruction of the density's own subcell means."""
+    pb = W.euler_entropy_wave(6, seed=12)
+    o = oracle.Oracle(pb, k=2, limiter=2)
+    u = o.project(pb.u0)
+    area = W.cell_areas(pb.mesh)
+    for c in (3, 17, 40):
+        out, st = o.limit_cell(u, c)
+        assert st == 0
+        d = out[0, 1:]
+        scale = np.abs(d).max()
+        assert scale > 1e-4
+        assert np.abs(out[1, 1:] - 0.7 * d).max() < 1e-12 * scale
+        assert np.abs(out[2, 1:] - 0.3 * d).max() < 1e-12 * scale
+        assert np.abs(out[3, 1:] - 0.5 * (0.7 ** 2 + 0.3 ** 2) * d).max() < 1e-12 * scale
+        sm = o.subcell_means(u, c)
+        w = o.weno(c, u[c, 0, 0] / np.sqrt(area[c]), sm[:, :3, 0], sm[:, 3:7, 0])
+        assert np.abs(d - w["modes"][1:]).max() < 1e-11 * scale
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_euler_characteristic_reconstruction_identities(k):
+    """SURVEY C12 (reading R-char): with the linear weights the reconstruction is
+    linear in the data, so transforming by L_d, reconstructing each field and
+    mapping back by R_d (then averaging x and y) must equal reconstructing each
+    conserved variable on its own, for any data (the eigenvector pair must be
+    inverse to each other for this to hold), and must return the data's own
+    modes for data that are one polynomial of degree <= k across the stencil
+    (cells whose three neighbours are interior)."""
+    pb = _transmissive_box_euler(7)
+    o = oracle.Oracle(pb, k=k, limiter=2)
+    area = W.cell_areas(pb.mesh)
+    np_ = (k + 1) * (k + 2) // 2
+    rng = np.random.default_rng(31 + k)
+    base = W.prim_to_cons(np.array([1.2]), 0.2, -0.1, 1.5)[0]
+    u = W.random_modes(pb.mesh, 4, np_, 33 + k, scale=0.02)
+    u[:, :, 0] += base[None, :] * np.sqrt(area)[:, None]
+    nb = o.connectivity()[0]
+    inner = [c for c in range(pb.mesh.nc) if np.all(nb[c] >= 0)][:6]
+    for c in inner:
+        out, st = o.limit_cell_linear(u, c)
+        sm = o.subcell_means(u, c)
+        for v in range(4):
+            w = o.weno(c, u[c, v, 0] / np.sqrt(area[c]), sm[:, :3, v], sm[:, 3:7, v] if k == 2 else None,
+                       force_linear=True)
+            assert np.abs(out[v, 1:] - w["modes"][1:]).max() < 1e-12 * np.abs(u[c]).max(), (c, v)
+    coef = rng.normal(size=(4, (k + 1) * (k + 2) // 2 - 1)) * 0.1
+    exps = [(d - e, e) for d in range(1, k + 1) for e in range(d + 1)]
+
+    def poly(x, y):
+        cols = [base[v] + sum(cf * x ** a * y ** b for cf, (a, b) in zip(coef[v], exps)) for v in range(4)]
+        return np.stack(cols, axis=1)
+
+    up = o.project(poly)
+    for c in inner:
+        out, st = o.limit_cell_linear(up, c)
+        assert st == 0
+        assert np.abs(out - up[c]).max() < 1e-11 * np.abs(up[c]).max(), c
+
+
+def _transmissive_box_euler(n):
+    mesh = W.split_square_mesh(n, n, 0.0, 1.0, 0.0, 1.0, 5, tag_fn=lambda side, xm, ym: 2)
+    return W.Problem("box", 1, mesh, None, {2: (W.TRANSMISSIVE, [])})
