@@ -55,7 +55,7 @@ enum { CSWDG_LIMITER_OFF = 0, CSWDG_LIMITER_KXRCF = 1, CSWDG_LIMITER_ALL = 2 };
 enum {
     CSWDG_BC_PERIODIC = 0,     /* paired by translation (mesh_upload `period`) */
     CSWDG_BC_DIRICHLET = 1,    /* params: nvar constant conserved values */
-    CSWDG_BC_TRANSMISSIVE = 2, /* ghost = interior trace */
+    CSWDG_BC_TRANSMISSIVE = 2, /* flux: the cell mean as the outside state; detection and stencil: interior trace */
     CSWDG_BC_WALL = 3,         /* Euler: interior trace with the normal momentum reversed */
     CSWDG_BC_SHOCKLINE = 4     /* params: x0, cot, speed, A[nvar], B[nvar];
                                   ghost = A where x < x0 + y*cot + speed*t, else B */
@@ -73,7 +73,9 @@ typedef struct {
                           the threshold.  CSWDG_FP32: as FP32_BULK with the
                           smoothness indicators and weights in float too (quotient
                           forms that stay inside the float range) */
-    int32_t limiter;   /* CSWDG_LIMITER_*: off, KXRCF-detected cells (Sec. 3.1), every cell */
+    int32_t limiter;   /* CSWDG_LIMITER_*: off, troubled cells (Sec. 3.1 KXRCF with ||U_j|| the cell's L2
+                          norm over its normalised measure; Euler cells whose polynomial has a
+                          non-positive density or pressure at a quadrature point), every cell */
     double c_k;        /* KXRCF threshold C_K (Sec. 3.1 takes 1) */
     double cfl;        /* time-step factor of the CFL rule used when dt <= 0 */
     double gamma;      /* ratio of specific heats (1.4) */

@@ -97,3 +97,31 @@ def test_bounded_wait_timeout_is_a_status(csw, cuda_stream):
     uo, _, st = o.step(u, 0.0, dt)
     assert st == 0 and rel(s.read_modes(), uo) < 1e-11
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_positivity_trigger_matches_the_oracle(csw, cuda_stream, precision):
+    """Reading R-pos as a detection trigger: a gas at rest (no inflow face, so
+    KXRCF gives R = 0) with one cell whose polynomial is negative at some
+    quadrature points.  The GPU flags exactly that cell, like the oracle, and
+    reconstructs it to the oracle's modes (FP64: 1e-11; FP32-bulk: float
+    rounding of the state)."""
+    pb = W.euler_entropy_wave(6, seed=12)
+    o = oracle.Oracle(pb, k=2, limiter=1)
+    area = W.cell_areas(pb.mesh)
+    base = W.prim_to_cons(np.array([1.0]), 0.0, 0.0, 1.0)[0]
+    u = np.zeros((pb.mesh.nc, 4, 6))
+    u[:, :, 0] = base[None, :] * np.sqrt(area)[:, None]
+    c = 11
+    u[c, 0, 1] = 2.0 * u[c, 0, 0]
+    u[c, 3, 2] = -1.5 * u[c, 3, 0]
+    fo, R = o.detect(u)
+    assert fo[c] == 1 and R[c] == 0.0 and fo.sum() == 1
+    lo, st = o.limit_cell(u, c)
+    s = csw.Solver(csw.EULER, 2, precision, csw.LIMITER_KXRCF, stream=cuda_stream)
+    s.setup(pb)
+    ug, fg = s.limit(u, 0.0)
+    assert np.array_equal(fg, fo)
+    tol = 1e-11 if precision == 0 else 1e-6
+    assert np.abs(ug[c] - lo).max() < tol * np.abs(lo).max()
+    s.close()

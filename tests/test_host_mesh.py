@@ -8,7 +8,8 @@ the CPU: the properties the stage kernel relies on.
   two cells obtain exact negatives only with exactly opposite normals.
 * |n~| = 2 |e| / |K| describes one edge length from both sides.
 * The internal order is a permutation of the caller's cells, and the cell
-  geometry matches the caller's triangle it came from.
+  geometry (inverse Jacobian, KXRCF scale) matches the caller's triangle it
+  came from.
 """
 import dataclasses
 
@@ -68,6 +69,12 @@ def test_host_mesh_faces_and_normals(cswdg, name, pb, k):
         e1 = nl[inner] * area[inner] / 2
         e2 = geo[G_N0L + 3 * f2, c2] * area[c2] / 2
         assert np.allclose(e1, e2, rtol=1e-13, atol=0)
+    # KXRCF scale (Sec. 3.1 with h the circumradius, reading R-kxrcf): kappa = h^{(k+1)/2} / sqrt(2),
+    # the stored coefficients being sqrt(2/|K|) times the orthonormal ones
+    c = b - a
+    la, lb, lc = np.hypot(*a.T), np.hypot(*b.T), np.hypot(*c.T)
+    hc = la * lb * lc / (4.0 * area)
+    assert np.allclose(geo[13], hc ** ((k + 1) / 2) / np.sqrt(2.0), rtol=1e-12, atol=0)
     # each interior face is seen twice; boundary faces have negative codes
     assert ninterior % 2 == 0
     assert (nbr < 0).sum() == len(pb.mesh.bface) or pb.mesh.period is not None

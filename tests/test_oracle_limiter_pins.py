@@ -242,7 +242,7 @@ def test_positivity_trigger_and_fallback():
 
 
 def test_euler_characteristic_fields_isolate_the_entropy_wave():
-    """SURVEY C12 / Sec. 3.2 last paragraph (reading R-char), field isolation:
+    """Sec. 3.2, last paragraph (reading R-char), field isolation:
     entropy-wave data (only the density varies; u = 0.7, v = 0.3, p = 1) lie
     along the entropy eigenvector (1, u, v, |v|^2/2), which is the same for the
     x and y directions, so in both characteristic decompositions one field
@@ -270,7 +270,7 @@ def test_euler_characteristic_fields_isolate_the_entropy_wave():
 
 @pytest.mark.parametrize("k", [1, 2])
 def test_euler_characteristic_reconstruction_identities(k):
-    """SURVEY C12 (reading R-char): with the linear weights the reconstruction is
+    """Sec. 3.2, last paragraph (reading R-char): with the linear weights the reconstruction is
     linear in the data, so transforming by L_d, reconstructing each field and
     mapping back by R_d (then averaging x and y) must equal reconstructing each
     conserved variable on its own, for any data (the eigenvector pair must be
