@@ -199,21 +199,29 @@ cswdg_status cswdg_adjoint_steps(cswdg_solver *s, double dt, int64_t nsteps, int
 /* Launch-shape autotuner for the stage kernel (operator + RK update; no
  * counterpart in the paper).  Times CSWDG_TUNE_CANDIDATES shapes -- cells per
  * block 64/128/256, one block per tile of cells or a persistent grid of
- * (SMs x resident blocks) -- on the current state and keeps the fastest for
- * later steps.  Call after the initial condition is set.  ms_host (nullable,
- * CSWDG_TUNE_CANDIDATES doubles): mean kernel time of each candidate in the
- * order 64, 128, 256 (one block per tile), 64 x 8, 128 x 4, 256 x 2,
- * 128 x 8 blocks per SM; chosen_host (nullable, 2 int32): cells per block and
- * grid (0 = one block per tile).  The state is not changed.
+ * (SMs x resident blocks), every cell computing its three faces or each face
+ * computed once per tile (tile_faces, see cswdg_set_stage_shape) -- on the
+ * current state and keeps the fastest for later steps.  Call after the
+ * initial condition is set.  ms_host (nullable, CSWDG_TUNE_CANDIDATES
+ * doubles): mean kernel time of each candidate in the order 64, 128, 256 (one
+ * block per tile), 64 x 8, 128 x 4, 256 x 2, 128 x 8 blocks per SM, then with
+ * tile_faces 128, 256 (one block per tile), 128 x 4, 256 x 2 blocks per SM.
+ * chosen_host (nullable, 3 int32): cells per block, grid (0 = one block per
+ * tile), tile_faces (0/1).  The state is not changed.
  * Errors: EINVAL (no mesh), ECUDA. */
-#define CSWDG_TUNE_CANDIDATES 7
+#define CSWDG_TUNE_CANDIDATES 11
 cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_host);
 
 /* Set the stage kernel's launch shape directly: cells per block (64, 128 or
- * 256) and the number of blocks (0: one block per tile of cells; > 0: that
- * many blocks, each looping over tiles).  Results do not depend on the shape.
- * Errors: EINVAL. */
-cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid);
+ * 256), the number of blocks (0: one block per tile of cells; > 0: that
+ * many blocks, each looping over tiles) and tile_faces (0: every cell
+ * evaluates its three face integrals, forming its neighbours' traces from
+ * their modes; 1: a block first writes its cells' traces at the face points to
+ * shared memory, then computes the flux of each face between two of its cells
+ * once (and of each face to another tile or the boundary from the traces and
+ * ghosts as before), 128 or 256 cells per block).  Results do not depend on
+ * the shape: the two variants agree bit for bit.  Errors: EINVAL. */
+cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid, int32_t tile_faces);
 
 /* Self-test of the device error path (no counterpart in the paper): launches
  * one warp that waits, with the wait primitive of the reconstruction kernel's
@@ -276,7 +284,10 @@ cswdg_status cswdg_cfl_dt(cswdg_solver *s, double *dt_host);
 /* Device-pointer variant of one SSP-RK3 stage for callers that manage their
  * own buffers: out = a*un + b*(uprev + dt*L_h(uprev)) at time t_rhs, in the
  * library's internal layout (see cswdg_internal_layout) and precision.
- * un_dev may be NULL when a == 0.  No limiter.  Errors: EINVAL, ECUDA. */
+ * un_dev may be NULL when a == 0.  The kernels move cells in 16-byte vectors:
+ * every pointer must be 16-byte aligned (cudaMalloc's are), else EINVAL.
+ * out_dev must not overlap uprev_dev (other cells read it during the stage);
+ * it may equal un_dev.  No limiter.  Errors: EINVAL, ECUDA. */
 cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un_dev, const void *uprev_dev, void *out_dev,
                              double a, double b, double dt, double t_rhs);
 

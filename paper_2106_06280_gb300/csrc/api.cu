@@ -434,6 +434,7 @@ cswdg_status cswdg_mesh_upload(cswdg_solver *s, int64_t nv, const double *xy, in
     cudaError_t e = cudaSuccess;
     auto A_ = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
     A_(cudaGetDevice(&s->device));
+    A_(stage_kernels_prepare());
     A_(cudaMalloc(&s->U, nstate * rs));
     A_(cudaMalloc(&s->A, nstate * rs));
     A_(cudaMalloc(&s->B, nstate * rs));
@@ -830,6 +831,9 @@ cswdg_status cswdg_cfl_dt(cswdg_solver *s, double *dt)
 cswdg_status cswdg_stage_dev(cswdg_solver *s, const void *un, const void *uprev, void *out, double a, double b, double dt, double t_rhs)
 {
     if (!s || !s->mesh_ready || !uprev || !out || (a != 0.0 && !un)) return fail(s, CSWDG_EINVAL, "stage_dev");
+    auto misaligned = [](const void *p) { return ((uintptr_t)p & 15u) != 0; };
+    if (misaligned(uprev) || misaligned(out) || (a != 0.0 && misaligned(un)))
+        return fail(s, CSWDG_EINVAL, "stage_dev: device pointers must be 16-byte aligned");
     Ctl h;
     if (cswdg_status r = read_ctl(s, &h)) return r;
     Ctl w = h;
@@ -881,8 +885,9 @@ cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_ho
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const StageShape cand[CSWDG_TUNE_CANDIDATES] = {{64, 0},        {128, 0},       {256, 0},      {64, nsm * 8},
-                                                    {128, nsm * 4}, {256, nsm * 2}, {128, nsm * 8}};
+    const StageShape cand[CSWDG_TUNE_CANDIDATES] = {{64, 0, 0},       {128, 0, 0},       {256, 0, 0},       {64, nsm * 8, 0},
+                                                    {128, nsm * 4, 0}, {256, nsm * 2, 0}, {128, nsm * 8, 0}, {128, 0, 1},
+                                                    {256, 0, 1},       {128, nsm * 4, 1}, {256, nsm * 2, 1}};
     Ctl h;
     if (cswdg_status r = read_ctl(s, &h)) return r;
     Ctl w = h;
@@ -913,16 +918,19 @@ cswdg_status cswdg_autotune(cswdg_solver *s, double *ms_host, int32_t *chosen_ho
     s->shape = cand[ib];
     for (int i = 0; i < 2; ++i)
         if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
-    if (chosen_host) { chosen_host[0] = cand[ib].blk; chosen_host[1] = cand[ib].grid; }
+    if (chosen_host) { chosen_host[0] = cand[ib].blk; chosen_host[1] = cand[ib].grid; chosen_host[2] = cand[ib].tile_faces; }
     return write_ctl(s, &h);
 }
 
-cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid)
+cswdg_status cswdg_set_stage_shape(cswdg_solver *s, int32_t cells_per_block, int32_t grid, int32_t tile_faces)
 {
-    if (!s || (cells_per_block != 64 && cells_per_block != 128 && cells_per_block != 256) || grid < 0)
-        return fail(s, CSWDG_EINVAL, "set_stage_shape: cells per block 64, 128 or 256; grid >= 0");
+    if (!s || (cells_per_block != 64 && cells_per_block != 128 && cells_per_block != 256) || grid < 0 ||
+        (tile_faces != 0 && tile_faces != 1) || (tile_faces == 1 && cells_per_block == 64))
+        return fail(s, CSWDG_EINVAL,
+                    "set_stage_shape: cells per block 64, 128 or 256 (128 or 256 with tile_faces); grid >= 0; tile_faces 0 or 1");
     s->shape.blk = cells_per_block;
     s->shape.grid = grid;
+    s->shape.tile_faces = tile_faces;
     for (int i = 0; i < 2; ++i)
         if (s->graph[i]) { cudaGraphExecDestroy(s->graph[i]); s->graph[i] = nullptr; }
     return CSWDG_OK;

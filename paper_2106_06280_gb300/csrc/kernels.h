@@ -28,11 +28,16 @@ cudaError_t operator_upload_tables();
 cudaError_t limiter_upload_tables();
 cudaError_t adjoint_upload_tables();
 
-// launch shape of the stage kernel: cells per block (64, 128, 256) and the
-// number of blocks (0: one block per tile of cells; > 0: a persistent grid)
+// launch shape of the stage kernel: cells per block (64, 128, 256), the
+// number of blocks (0: one block per tile of cells; > 0: a persistent grid) and
+// the variant (tile_faces 0: k_stage, every cell computes its three faces;
+// 1: k_stage_tiles, each face once per tile, 128 or 256 cells per block)
 struct StageShape {
-    int blk = 128, grid = 0;
+    int blk = 128, grid = 0, tile_faces = 0;
 };
+// sets the dynamic shared memory limits of the tile-shared stage kernels on
+// the current device
+cudaError_t stage_kernels_prepare();
 template <typename R>
 void launch_stage(int eq, int k, const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac,
                   int lam_next, R *kx, Ctl *ctl, StageShape sh, cudaStream_t st);

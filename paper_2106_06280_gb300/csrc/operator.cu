@@ -99,12 +99,9 @@ __device__ __forceinline__ void trace(const R (&a0)[NV], const R (&a)[NV][NP], c
 // one face point: twice the LLF flux between this cell's trace Ui (first) and
 // the other side's Uo, through this cell's outward normal, weighted by
 // wgt = w_g |n~| / 2 and taken off the residual against psi_i at the point
-template <int EQ, int NV, int NP, typename R>
-__device__ __forceinline__ void face_point(const R (&Ui)[NV], const R (&Uo)[NV], R nx, R ny, R gam, R wgt,
-                                           const R *__restrict__ phi, R (&acc)[NV][NP])
+template <int NV, int NP, typename R>
+__device__ __forceinline__ void face_scatter(const R (&F)[NV], R wgt, const R *__restrict__ phi, R (&acc)[NV][NP])
 {
-    R F[NV];
-    llf2<EQ, R>(Ui, Uo, nx, ny, gam, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const R wf = wgt * F[v];
@@ -113,11 +110,117 @@ __device__ __forceinline__ void face_point(const R (&Ui)[NV], const R (&Uo)[NV],
     }
 }
 
+template <int EQ, int NV, int NP, typename R>
+__device__ __forceinline__ void face_point(const R (&Ui)[NV], const R (&Uo)[NV], R nx, R ny, R gam, R wgt,
+                                           const R *__restrict__ phi, R (&acc)[NV][NP])
+{
+    R F[NV];
+    llf2<EQ, R>(Ui, Uo, nx, ny, gam, F);
+    face_scatter<NV, NP, R>(F, wgt, phi, acc);
+}
+
 // Stage kernel: out = ca*un + cb*up + (cl*dt)*L_h(up), L_h at t + tfac*dt.
 // One thread per cell; each cell evaluates its volume integral and all three
 // face integrals (the neighbour's trace is read from its modes), so no face
 // buffer, colouring or atomics are needed.
 // ---------------------------------------------------------------------------
+// end of a cell's stage: the RK combination res = ca*un + cb*u + (cl*dt)*acc,
+// its store, the KXRCF precursors of the new state (kx set) and, when lam_next
+// is set, the largest wave speed of the new mean (else 0).  fg: (nx, ny, |n~|)
+// of faces 0-2; fc0-fc2: neighbour codes; nbf: the neighbours' local faces.
+template <int EQ, int K, typename R>
+__device__ __forceinline__ R stage_finish(const MeshDev<R> &M, const R *un, R *out, R ca, R cb, R cl, int lam_next,
+                                          R *__restrict__ kx, Ctl *__restrict__ ctl, int c,
+                                          const R (&u)[Eqn<EQ>::NV][Deg<K>::NP], const R (&acc)[Eqn<EQ>::NV][Deg<K>::NP],
+                                          const R (&fg)[9], int fc0, int fc1, int fc2, unsigned nbf)
+{
+    constexpr int NP = Deg<K>::NP, NV = Eqn<EQ>::NV;
+    const Tab<R, K> &T = tab<R, K>();
+    const R gam = M.gammar;
+    const R cdt = cl * ((sizeof(R) == 4) ? (R)ctl->dtf : (R)ctl->dt);
+    R res[NV][NP];
+    if (un) {
+        R w[NV][NP];
+        load_cell<NV, NP>(un, c, w);
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m] + ca * w[v][m];
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m];
+    }
+    {
+        store_cell<NV, NP>(out, c, res);
+        // KXRCF precursors of the new state for the detection that follows
+        if (kx) {
+            R k7[KX_COUNT];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                R s = R(0);
+#pragma unroll
+                for (int m = 0; m < NP; ++m) s += res[0][m] * T.fint[f][m];
+                k7[KX_I0 + f] = s;
+            }
+            R n2 = R(0);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
+            // reading R-pos: a polynomial that is non-physical at a quadrature point
+            // makes the cell troubled.  Only the cheap bound runs here (one thread per
+            // cell: the point-by-point check would stall whole warps); a cell that fails
+            // it is handed to the detection as a candidate by a negated norm (n2 > 0
+            // for any cell with a positive mean density)
+            if constexpr (EQ == EULER)
+                if (!physical_by_bound<K, R>(res, T)) n2 = -n2;
+            k7[KX_NRM2] = n2;
+            // the new means: physically admissible (Euler: rho > 0, p > 0; screened
+            // in the state precision, close calls in double), and the mean velocity
+            // direction (the momentum) that decides the inflow faces
+            R vx, vy;
+            if (EQ == EULER) {
+                const R r = res[0][0], mx = res[1][0], my = res[2][0], E = res[NV - 1][0];
+                const R q = R(2) * E * r - (mx * mx + my * my);
+                bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
+                if (!ok && !(q != q)) {
+                    const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
+                    ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
+                }
+                if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
+                vx = mx;
+                vy = my;
+            } else {
+                vx = vy = res[0][0];
+                if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
+            }
+            // inflow weights: v.n < 0 (uncontracted, as a plain evaluation decides it)
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const R nx = fg[3 * f], ny = fg[3 * f + 1], nl = fg[3 * f + 2];
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
+                k7[KX_W0 + f] = (vn < R(0)) ? ((code >= 0) ? nl : -nl) : R(0);
+            }
+            store_kx<R>(kx, c, k7);
+            // this cell's face means also go to the neighbours' records, at the
+            // slot of the shared face, so that the detection reads no neighbour
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                if (code >= 0) kx[(size_t)code * KX_STRIDE + KX_O0 + ((nbf >> (2 * f)) & 3)] = k7[KX_I0 + f];
+            }
+        }
+    }
+    // last stage of a step: the largest wave speed of the new means, for the next
+    // step's CFL rule (the reconstruction that follows keeps every cell mean)
+    if (!lam_next) return R(0);
+    R mn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) mn[v] = res[v][0];
+    return mean_wave_speed<EQ, R>(mn, gam);
+}
+
 // one cell of the stage; returns the largest wave speed of its new mean when
 // lam_next is set (else 0)
 template <int EQ, int K, typename R>
@@ -213,88 +316,7 @@ __device__ __forceinline__ R stage_cell(const MeshDev<R> &M, const R *un, const 
         }
     }
 
-    const R cdt = cl * ((sizeof(R) == 4) ? (R)ctl->dtf : (R)ctl->dt);
-    R res[NV][NP];
-    if (un) {
-        R w[NV][NP];
-        load_cell<NV, NP>(un, c, w);
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m] + ca * w[v][m];
-    } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int m = 0; m < NP; ++m) res[v][m] = cb * u[v][m] + cdt * acc[v][m];
-    }
-    {
-        store_cell<NV, NP>(out, c, res);
-        // KXRCF precursors of the new state for the detection that follows
-        if (kx) {
-            R k7[KX_COUNT];
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                R s = R(0);
-#pragma unroll
-                for (int m = 0; m < NP; ++m) s += res[0][m] * T.fint[f][m];
-                k7[KX_I0 + f] = s;
-            }
-            R n2 = R(0);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) n2 += res[0][m] * res[0][m];
-            // reading R-pos: a polynomial that is non-physical at a quadrature point
-            // makes the cell troubled.  Only the cheap bound runs here (one thread per
-            // cell: the point-by-point check would stall whole warps); a cell that fails
-            // it is handed to the detection as a candidate by a negated norm (n2 > 0
-            // for any cell with a positive mean density)
-            if constexpr (EQ == EULER)
-                if (!physical_by_bound<K, R>(res, T)) n2 = -n2;
-            k7[KX_NRM2] = n2;
-            // the new means: physically admissible (Euler: rho > 0, p > 0; screened
-            // in the state precision, close calls in double), and the mean velocity
-            // direction (the momentum) that decides the inflow faces
-            R vx, vy;
-            if (EQ == EULER) {
-                const R r = res[0][0], mx = res[1][0], my = res[2][0], E = res[NV - 1][0];
-                const R q = R(2) * E * r - (mx * mx + my * my);
-                bool ok = (r > R(0)) && (q > R(1e-3) * (R(2) * E * r));
-                if (!ok && !(q != q)) {
-                    const double rd = (double)r, mxd = (double)mx, myd = (double)my, Ed = (double)E;
-                    ok = (rd > 0.0) && (2.0 * Ed * rd - (mxd * mxd + myd * myd) > 0.0);
-                }
-                if (!ok) atomicOr(&ctl->err, ERR_NONPHYS);
-                vx = mx;
-                vy = my;
-            } else {
-                vx = vy = res[0][0];
-                if (!(vx == vx)) atomicOr(&ctl->err, ERR_NONPHYS);
-            }
-            // inflow weights: v.n < 0 (uncontracted, as a plain evaluation decides it)
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const R nx = fg[3 * f], ny = fg[3 * f + 1], nl = fg[3 * f + 2];
-                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
-                const R vn = (EQ == BURGERS) ? vx * radd_rn(nx, ny) : radd_rn(rmul_rn(vx, nx), rmul_rn(vy, ny));
-                k7[KX_W0 + f] = (vn < R(0)) ? ((code >= 0) ? nl : -nl) : R(0);
-            }
-            store_kx<R>(kx, c, k7);
-            // this cell's face means also go to the neighbours' records, at the
-            // slot of the shared face, so that the detection reads no neighbour
-#pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
-                if (code >= 0) kx[(size_t)code * KX_STRIDE + KX_O0 + ((nbf >> (2 * f)) & 3)] = k7[KX_I0 + f];
-            }
-        }
-    }
-    // last stage of a step: the largest wave speed of the new means, for the next
-    // step's CFL rule (the reconstruction that follows keeps every cell mean)
-    if (!lam_next) return R(0);
-    R mn[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) mn[v] = res[v][0];
-    return mean_wave_speed<EQ, R>(mn, gam);
+    return stage_finish<EQ, K, R>(M, un, out, ca, cb, cl, lam_next, kx, ctl, c, u, acc, fg, fc0, fc1, fc2, nbf);
 }
 
 // Stage kernel: tiles of BLK consecutive cells (Morton order), one thread per
@@ -319,6 +341,273 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
     if (lam_next) block_max_to_ctl<R>(lam, ctl);  // every thread of the block gets here
 }
 
+// ---------------------------------------------------------------------------
+// Tile-shared stage kernel: the same stage as k_stage, with each face's work
+// done once per tile.  A block takes a tile of BLK consecutive cells (Morton
+// order) in three phases separated by block barriers:
+//   1. every cell writes its traces at its 3 x QF face points to the shared
+//      array S (slot (f, g) of cell a at S[((f * QF + g) * BLK + a) * NV]);
+//   2. a face-parallel pass over the tile's face list.  A face between two
+//      cells of the tile (listed once, by its lower-index cell a) reads both
+//      traces and computes 2F = llf2(U_a, U_b, n_a) once: F goes into a's slot
+//      and -F into b's slot at the matching point, which is what b's own call
+//      llf2(U_b, U_a, -n_a) returns bit for bit (each slot belongs to one face,
+//      so fluxes overwrite traces in place).  Where b's stored normal is not
+//      the exact negative of a's (a periodic face), b's flux is computed from
+//      its own normal.  A face to a cell of another tile forms that cell's
+//      trace from its modes, a boundary face its ghost, as k_stage does;
+//   3. every cell evaluates its volume integral, takes the fluxes off its
+//      residual from its own slots in k_stage's order and finishes the stage.
+// The list holds the tile's interior faces, then those to other tiles, then
+// the boundary faces, so the warps of the face pass mostly run one kind.  The
+// result equals k_stage's bit for bit.
+template <int NV, typename R> __device__ __forceinline__ void sput(R *s, const R (&U)[NV])
+{
+    if constexpr (NV == 4 && sizeof(R) == 4) {
+        *reinterpret_cast<float4 *>(s) = make_float4(U[0], U[1], U[2], U[3]);
+    } else if constexpr (NV == 4) {
+        reinterpret_cast<double2 *>(s)[0] = make_double2(U[0], U[1]);
+        reinterpret_cast<double2 *>(s)[1] = make_double2(U[2], U[3]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s[v] = U[v];
+    }
+}
+template <int NV, typename R> __device__ __forceinline__ void sget(const R *s, R (&U)[NV])
+{
+    if constexpr (NV == 4 && sizeof(R) == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(s);
+        U[0] = x.x; U[1] = x.y; U[2] = x.z; U[3] = x.w;
+    } else if constexpr (NV == 4) {
+        const double2 x = reinterpret_cast<const double2 *>(s)[0], y = reinterpret_cast<const double2 *>(s)[1];
+        U[0] = x.x; U[1] = x.y; U[2] = y.x; U[3] = y.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = s[v];
+    }
+}
+
+// shared memory of one block of the tile-shared kernel (bytes): the slots, the
+// face list (3 BLK entries) and the per-warp counts
+template <int EQ, int K, typename R> constexpr size_t tile_smem_bytes(int blk)
+{
+    return (size_t)3 * Deg<K>::QF * blk * Eqn<EQ>::NV * sizeof(R) + (size_t)3 * blk * sizeof(int) + 32 * sizeof(int);
+}
+
+template <int EQ, int K, typename R, int BLK>
+__global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
+    k_stage_tiles(MeshDev<R> M, const R *un, const R *__restrict__ up, R *out, R ca, R cb, R cl, double tfac, int lam_next,
+                  R *__restrict__ kx, Ctl *__restrict__ ctl)
+{
+    constexpr int NP = Deg<K>::NP, QV = Deg<K>::QV, QF = Deg<K>::QF, NV = Eqn<EQ>::NV;
+    static_assert(BLK <= 256, "face-list counts are packed in 10-bit fields");
+    extern __shared__ __align__(16) unsigned char tile_smem[];
+    R *S = reinterpret_cast<R *>(tile_smem);
+    int *jobs = reinterpret_cast<int *>(tile_smem + (size_t)3 * QF * BLK * NV * sizeof(R));
+    int *wtot = jobs + 3 * BLK;
+    auto slot = [&](int f, int g, int a) { return S + ((size_t)(f * QF + g) * BLK + a) * NV; };
+
+    if (!ctl->active) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nflag = 0;
+    const Tab<R, K> &T = tab<R, K>();
+    const int ld = M.ldc;
+    const R gam = M.gammar;
+    const R psi0 = T.vphi[0][0];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int ntiles = (M.nc + BLK - 1) / BLK;
+    R lam = R(0);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int c0 = tile * BLK, c = c0 + t;
+        const bool valid = c < M.nc;
+        R u[NV][NP];
+        R fg[9];
+        int fc0 = -1, fc1 = -1, fc2 = -1;
+        unsigned nbf = 0;
+        if (valid) {
+            load_cell<NV, NP>(up, c, u);
+            fc0 = M.nbr[c]; fc1 = M.nbr[ld + c]; fc2 = M.nbr[2 * ld + c];
+            nbf = M.nbf[c];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fg[i] = M.geo[(G_N0X + i) * ld + c];
+        }
+        // face list: counts of interior (taken by the lower-index cell), outer and
+        // boundary faces packed in 10-bit fields, one block-wide exclusive scan
+        unsigned cnt = 0;
+        if (valid) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                const int b = code - c0;
+                // a face to itself (b == t) goes to the outer list, computed per side
+                cnt += (code < 0) ? (1u << 20) : (b >= 0 && b < BLK && b != t) ? ((b > t) ? 1u : 0u) : (1u << 10);
+            }
+        }
+        unsigned inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wtot[warp] = (int)inc;
+        // phase 1: own traces at the face points
+        if (valid) {
+            R m0[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) m0[v] = u[v][0] * psi0;
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int g = 0; g < QF; ++g) {
+                    R Ui[NV];
+                    trace<NV, NP, R>(m0, u, T.fphi[f][g], Ui);
+                    sput<NV, R>(slot(f, g, t), Ui);
+                }
+        }
+        __syncthreads();
+        unsigned pre = 0, tot = 0;
+        for (int w = 0; w < BLK / 32; ++w) {
+            const unsigned x = (unsigned)wtot[w];
+            if (w < warp) pre += x;
+            tot += x;
+        }
+        const unsigned exc = pre + inc - cnt;
+        const int nint = (int)(tot & 1023u), nout = (int)((tot >> 10) & 1023u), nall = nint + nout + (int)(tot >> 20);
+        if (valid) {
+            int pi = (int)(exc & 1023u), po = nint + (int)((exc >> 10) & 1023u), pb = nint + nout + (int)(exc >> 20);
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+                const int b = code - c0, job = t | (f << 16);
+                if (code < 0) jobs[pb++] = job;
+                else if (b >= 0 && b < BLK && b != t) { if (b > t) jobs[pi++] = job; }
+                else jobs[po++] = job;
+            }
+        }
+        __syncthreads();
+        // phase 2: the face pass
+        for (int j = t; j < nall; j += BLK) {
+            const int a = jobs[j] & 0xffff, f = jobs[j] >> 16, ca_ = c0 + a;
+            const int code = M.nbr[f * ld + ca_];
+            const R nx = M.geo[(G_N0X + 3 * f) * ld + ca_], ny = M.geo[(G_N0Y + 3 * f) * ld + ca_];
+            if (j < nint) {
+                const int b = code - c0, nf = (M.nbf[ca_] >> (2 * f)) & 3;
+                const R bx = M.geo[(G_N0X + 3 * nf) * ld + code], by = M.geo[(G_N0Y + 3 * nf) * ld + code];
+                const bool mirrored = (bx == -nx) && (by == -ny);
+#pragma unroll
+                for (int g = 0; g < QF; ++g) {
+                    R Ua[NV], Ub[NV], F[NV];
+                    sget<NV, R>(slot(f, g, a), Ua);
+                    sget<NV, R>(slot(nf, QF - 1 - g, b), Ub);
+                    llf2<EQ, R>(Ua, Ub, nx, ny, gam, F);
+                    R Fb[NV];
+                    if (mirrored) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) Fb[v] = -F[v];
+                    } else {
+                        llf2<EQ, R>(Ub, Ua, bx, by, gam, Fb);
+                    }
+                    sput<NV, R>(slot(f, g, a), F);
+                    sput<NV, R>(slot(nf, QF - 1 - g, b), Fb);
+                }
+            } else if (j < nint + nout) {
+                const int nf = (M.nbf[ca_] >> (2 * f)) & 3;
+                R w[NV][NP], w0[NV];
+                load_cell<NV, NP>(up, code, w);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) w0[v] = w[v][0] * psi0;
+#pragma unroll
+                for (int g = 0; g < QF; ++g) {
+                    R Ua[NV], Ub[NV], F[NV];
+                    sget<NV, R>(slot(f, g, a), Ua);
+                    trace<NV, NP, R>(w0, w, T.fphi[nf][QF - 1 - g], Ub);
+                    llf2<EQ, R>(Ua, Ub, nx, ny, gam, F);
+                    sput<NV, R>(slot(f, g, a), F);
+                }
+            } else {
+                const BFace bf = M.bf[-code - 1];
+                const bool transmissive = M.bc->kind[bf.tag] == BC_TRANSMISSIVE;
+                R m0[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) m0[v] = up[((size_t)ca_ * NV + v) * NP] * psi0;
+#pragma unroll
+                for (int g = 0; g < QF; ++g) {
+                    R Ua[NV], Uo[NV], F[NV];
+                    sget<NV, R>(slot(f, g, a), Ua);
+                    if (transmissive) {
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) Uo[v] = m0[v];
+                    } else {
+                        ghost<EQ, R>(bf, M.bc, (double)T.ft[g], stage_time(ctl, tfac), Ua, Uo);
+                    }
+                    llf2<EQ, R>(Ua, Uo, nx, ny, gam, F);
+                    sput<NV, R>(slot(f, g, a), F);
+                }
+            }
+        }
+        __syncthreads();
+        // phase 3: volume integral, the fluxes from this cell's slots, the update
+        if (valid) {
+            R acc[NV][NP];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int m = 0; m < NP; ++m) acc[v][m] = R(0);
+            const R g0 = M.geo[G_RX * ld + c], g1 = M.geo[G_RY * ld + c], g2 = M.geo[G_SX * ld + c], g3 = M.geo[G_SY * ld + c];
+            R m0[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) m0[v] = u[v][0] * psi0;
+#pragma unroll
+            for (int q = 0; q < QV; ++q) {
+                R U[NV], f_[NV], g_[NV];
+                trace<NV, NP, R>(m0, u, T.vphi[q], U);
+                flux_fg<EQ, R>(U, gam, f_, g_);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const R Fr = g0 * f_[v] + g1 * g_[v];
+                    const R Fs = g2 * f_[v] + g3 * g_[v];
+#pragma unroll
+                    for (int m = 1; m < NP; ++m) acc[v][m] += (m > K) ? T.vdrw[q][m] * Fr + T.vdsw[q][m] * Fs : T.vdsw[q][m] * Fs;
+                }
+            }
+#pragma unroll 1
+            for (int f = 0; f < 3; ++f) {
+                const R hnl = R(0.5) * ((f == 0) ? fg[2] : (f == 1) ? fg[5] : fg[8]);
+#pragma unroll
+                for (int g = 0; g < QF; ++g) {
+                    R F[NV];
+                    sget<NV, R>(slot(f, g, t), F);
+                    face_scatter<NV, NP, R>(F, T.fw[g] * hnl, T.fphi[f][g], acc);
+                }
+            }
+            lam = rmax(lam, stage_finish<EQ, K, R>(M, un, out, ca, cb, cl, lam_next, kx, ctl, c, u, acc, fg, fc0, fc1, fc2, nbf));
+        }
+    }
+    if (lam_next) block_max_to_ctl<R>(lam, ctl);  // every thread of the block gets here
+}
+
+// dynamic shared memory limits of the tile-shared kernels (above the 48 KB
+// default for 256-cell tiles of the Euler state) on the current device
+template <int EQ, int K, typename R> cudaError_t tile_smem_attr()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_stage_tiles<EQ, K, R, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tile_smem_bytes<EQ, K, R>(128));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stage_tiles<EQ, K, R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)tile_smem_bytes<EQ, K, R>(256));
+}
+cudaError_t stage_kernels_prepare()
+{
+    cudaError_t e;
+    if ((e = tile_smem_attr<BURGERS, 1, float>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<BURGERS, 2, float>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<EULER, 1, float>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<EULER, 2, float>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<BURGERS, 1, double>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<BURGERS, 2, double>()) != cudaSuccess) return e;
+    if ((e = tile_smem_attr<EULER, 1, double>()) != cudaSuccess) return e;
+    return tile_smem_attr<EULER, 2, double>();
+}
+
 template <int EQ, int K, typename R>
 void launch_stage_t(const MeshDev<R> &M, const R *un, const R *up, R *out, R ca, R cb, R cl, double tfac, int lam_next, R *kx,
                     Ctl *ctl, StageShape sh, cudaStream_t st)
@@ -326,6 +615,12 @@ void launch_stage_t(const MeshDev<R> &M, const R *un, const R *up, R *out, R ca,
     const int blk = (sh.blk == 64 || sh.blk == 256) ? sh.blk : 128;
     const int ntiles = (M.nc + blk - 1) / blk;
     const int grd = (sh.grid > 0 && sh.grid < ntiles) ? sh.grid : ntiles;
+    if (sh.tile_faces && blk != 64) {
+        const size_t sm = tile_smem_bytes<EQ, K, R>(blk);
+        if (blk == 256) k_stage_tiles<EQ, K, R, 256><<<grd, 256, sm, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
+        else k_stage_tiles<EQ, K, R, 128><<<grd, 128, sm, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
+        return;
+    }
     if (blk == 64) k_stage<EQ, K, R, 64><<<grd, 64, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
     else if (blk == 256) k_stage<EQ, K, R, 256><<<grd, 256, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);
     else k_stage<EQ, K, R, 128><<<grd, 128, 0, st>>>(M, un, up, out, ca, cb, cl, tfac, lam_next, kx, ctl);

@@ -72,7 +72,7 @@ def _load():
         "cswdg_rhs_adjoint": ([vp, C.c_double, dp, dp, dp], C.c_int),
         "cswdg_adjoint_steps": ([vp, C.c_double, i64, i32, dp, dp, dp, dp, dp], C.c_int),
         "cswdg_limit_adjoint": ([vp, C.c_double, dp, dp, dp, C.POINTER(C.c_uint8)], C.c_int),
-        "cswdg_set_stage_shape": ([vp, i32, i32], C.c_int),
+        "cswdg_set_stage_shape": ([vp, i32, i32, i32], C.c_int),
         "cswdg_probe_fp64_fma": ([vp, dp], C.c_int),
         "cswdg_read_modes_f32": ([vp, C.POINTER(C.c_float)], C.c_int),
         "cswdg_write_modes_f32": ([vp, C.POINTER(C.c_float)], C.c_int),
@@ -94,7 +94,7 @@ EXPORTED = ["cswdg_create", "cswdg_destroy", "cswdg_last_error", "cswdg_set_boun
             "cswdg_autotune", "cswdg_rhs_adjoint", "cswdg_adjoint_steps", "cswdg_limit_adjoint",
             "cswdg_set_stage_shape", "cswdg_host_mesh", "cswdg_probe_fp64_fma",
             "cswdg_read_modes_f32", "cswdg_write_modes_f32"]
-TUNE_CANDIDATES = 7
+TUNE_CANDIDATES = 11
 
 
 def _d(a):
@@ -217,14 +217,14 @@ class Solver:
 
     def autotune(self):
         """Pick the stage kernel's launch shape on the current state; returns
-        (cells per block, grid or 0, per-candidate ms)."""
+        (cells per block, grid or 0, tile_faces 0/1, per-candidate ms)."""
         ms = np.zeros(TUNE_CANDIDATES)
-        ch = np.zeros(2, dtype=np.int32)
+        ch = np.zeros(3, dtype=np.int32)
         self._chk(lib.cswdg_autotune(self.h, _p(ms), ch.ctypes.data_as(C.POINTER(C.c_int32))))
-        return int(ch[0]), int(ch[1]), ms
+        return int(ch[0]), int(ch[1]), int(ch[2]), ms
 
-    def set_stage_shape(self, cells_per_block, grid=0):
-        self._chk(lib.cswdg_set_stage_shape(self.h, cells_per_block, grid))
+    def set_stage_shape(self, cells_per_block, grid=0, tile_faces=0):
+        self._chk(lib.cswdg_set_stage_shape(self.h, cells_per_block, grid, tile_faces))
 
     def launches_per_step(self, use_cfl=True):
         return int(lib.cswdg_launches_per_step(self.h, int(use_cfl)))

@@ -148,7 +148,8 @@ def test_project_ic_all_cells_limited(csw, cuda_stream):
         assert rel(ug[:, v], uo[:, v]) < TOL64
 
 
-@pytest.mark.parametrize("shape", [(64, 0), (128, 0), (256, 0), (64, 3), (128, 2), (256, 1)])
+@pytest.mark.parametrize("shape", [(64, 0), (128, 0), (256, 0), (64, 3), (128, 2), (256, 1),
+                                   (128, 0, 1), (256, 0, 1), (128, 2, 1), (256, 1, 1)])
 def test_stage_shapes_fp64(csw, cuda_stream, shape):
     """Every launch shape of the stage kernel (tiles of 64/128/256 cells, one
     block per tile or a small persistent grid looping over several tiles) gives
@@ -183,8 +184,9 @@ def test_autotune_keeps_results(csw, cuda_stream):
     s, o = make(csw, cuda_stream, pb, 2, 1)
     u = random_state(pb, 2, 501)
     s.write_modes(u)
-    blk, grid, ms = s.autotune()
-    assert blk in (64, 128, 256) and grid >= 0 and np.all(ms > 0)
+    blk, grid, tile_faces, ms = s.autotune()
+    assert blk in (64, 128, 256) and grid >= 0 and tile_faces in (0, 1) and np.all(ms > 0)
+    assert not (tile_faces and blk == 64)
     assert np.allclose(s.read_modes(), u, rtol=0, atol=1e-15 * np.abs(u).max())  # state untouched
     s.set_time(0.0)
     dt = 0.5 * o.cfl_dt(u, 0.1)
