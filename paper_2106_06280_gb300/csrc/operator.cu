@@ -388,10 +388,12 @@ template <int NV, typename R> __device__ __forceinline__ void sget(const R *s, R
 }
 
 // shared memory of one block of the tile-shared kernel (bytes): the slots, the
-// face list (3 BLK entries) and the per-warp counts
+// cells' face normals (3 BLK pairs), neighbour codes (3 BLK), the face list
+// (3 BLK entries) and the per-warp counts
 template <int EQ, int K, typename R> constexpr size_t tile_smem_bytes(int blk)
 {
-    return (size_t)3 * Deg<K>::QF * blk * Eqn<EQ>::NV * sizeof(R) + (size_t)3 * blk * sizeof(int) + 32 * sizeof(int);
+    return (size_t)3 * Deg<K>::QF * blk * Eqn<EQ>::NV * sizeof(R) + (size_t)6 * blk * sizeof(R) + (size_t)6 * blk * sizeof(int) +
+           32 * sizeof(int);
 }
 
 template <int EQ, int K, typename R, int BLK>
@@ -403,7 +405,9 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
     static_assert(BLK <= 256, "face-list counts are packed in 10-bit fields");
     extern __shared__ __align__(16) unsigned char tile_smem[];
     R *S = reinterpret_cast<R *>(tile_smem);
-    int *jobs = reinterpret_cast<int *>(tile_smem + (size_t)3 * QF * BLK * NV * sizeof(R));
+    R *nrm = S + (size_t)3 * QF * BLK * NV;  // (nx, ny) of face f of cell a at nrm[2 (f BLK + a)]
+    int *codes = reinterpret_cast<int *>(nrm + 6 * BLK);  // neighbour code of face f of cell a at codes[f BLK + a]
+    int *jobs = codes + 3 * BLK;
     int *wtot = jobs + 3 * BLK;
     auto slot = [&](int f, int g, int a) { return S + ((size_t)(f * QF + g) * BLK + a) * NV; };
 
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
         const int c0 = tile * BLK, c = c0 + t;
         const bool valid = c < M.nc;
         R u[NV][NP];
-        R fg[9];
+        R fg[9], g0 = R(0), g1 = R(0), g2 = R(0), g3 = R(0);
         int fc0 = -1, fc1 = -1, fc2 = -1;
         unsigned nbf = 0;
         if (valid) {
@@ -429,6 +433,13 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
             nbf = M.nbf[c];
 #pragma unroll
             for (int i = 0; i < 9; ++i) fg[i] = M.geo[(G_N0X + i) * ld + c];
+            g0 = M.geo[G_RX * ld + c]; g1 = M.geo[G_RY * ld + c]; g2 = M.geo[G_SX * ld + c]; g3 = M.geo[G_SY * ld + c];
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                nrm[2 * (f * BLK + t)] = fg[3 * f];
+                nrm[2 * (f * BLK + t) + 1] = fg[3 * f + 1];
+                codes[f * BLK + t] = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
+            }
         }
         // face list: counts of interior (taken by the lower-index cell), outer and
         // boundary faces packed in 10-bit fields, one block-wide exclusive scan
@@ -477,7 +488,10 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
 #pragma unroll
             for (int f = 0; f < 3; ++f) {
                 const int code = (f == 0) ? fc0 : (f == 1) ? fc1 : fc2;
-                const int b = code - c0, job = t | (f << 16);
+                // entry: cell a (8 bits), face f (2), the neighbour's local face nf (2),
+                // the neighbour's index in the tile b (8; interior faces)
+                const int b = code - c0, nf = (int)((nbf >> (2 * f)) & 3u);
+                const int job = t | (f << 8) | (nf << 10) | ((b & 255) << 12);
                 if (code < 0) jobs[pb++] = job;
                 else if (b >= 0 && b < BLK && b != t) { if (b > t) jobs[pi++] = job; }
                 else jobs[po++] = job;
@@ -486,12 +500,12 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
         __syncthreads();
         // phase 2: the face pass
         for (int j = t; j < nall; j += BLK) {
-            const int a = jobs[j] & 0xffff, f = jobs[j] >> 16, ca_ = c0 + a;
-            const int code = M.nbr[f * ld + ca_];
-            const R nx = M.geo[(G_N0X + 3 * f) * ld + ca_], ny = M.geo[(G_N0Y + 3 * f) * ld + ca_];
+            const int job = jobs[j];
+            const int a = job & 255, f = (job >> 8) & 3, nf = (job >> 10) & 3, ca_ = c0 + a;
+            const R nx = nrm[2 * (f * BLK + a)], ny = nrm[2 * (f * BLK + a) + 1];
             if (j < nint) {
-                const int b = code - c0, nf = (M.nbf[ca_] >> (2 * f)) & 3;
-                const R bx = M.geo[(G_N0X + 3 * nf) * ld + code], by = M.geo[(G_N0Y + 3 * nf) * ld + code];
+                const int b = (job >> 12) & 255;
+                const R bx = nrm[2 * (nf * BLK + b)], by = nrm[2 * (nf * BLK + b) + 1];
                 const bool mirrored = (bx == -nx) && (by == -ny);
 #pragma unroll
                 for (int g = 0; g < QF; ++g) {
@@ -510,7 +524,7 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
                     sput<NV, R>(slot(nf, QF - 1 - g, b), Fb);
                 }
             } else if (j < nint + nout) {
-                const int nf = (M.nbf[ca_] >> (2 * f)) & 3;
+                const int code = codes[f * BLK + a];
                 R w[NV][NP], w0[NV];
                 load_cell<NV, NP>(up, code, w);
 #pragma unroll
@@ -524,7 +538,7 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
                     sput<NV, R>(slot(f, g, a), F);
                 }
             } else {
-                const BFace bf = M.bf[-code - 1];
+                const BFace bf = M.bf[-codes[f * BLK + a] - 1];
                 const bool transmissive = M.bc->kind[bf.tag] == BC_TRANSMISSIVE;
                 R m0[NV];
 #pragma unroll
@@ -552,7 +566,6 @@ __global__ void __launch_bounds__(BLK, (sizeof(R) == 4) ? 512 / BLK : 1)
             for (int v = 0; v < NV; ++v)
 #pragma unroll
                 for (int m = 0; m < NP; ++m) acc[v][m] = R(0);
-            const R g0 = M.geo[G_RX * ld + c], g1 = M.geo[G_RY * ld + c], g2 = M.geo[G_SX * ld + c], g3 = M.geo[G_SY * ld + c];
             R m0[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) m0[v] = u[v][0] * psi0;

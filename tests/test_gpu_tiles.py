@@ -106,3 +106,22 @@ def test_tile_shape_rejects_64(csw, cuda_stream):
     with pytest.raises(RuntimeError):
         s.set_stage_shape(64, 0, 1)
     s.close()
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (1, 2), (2, 2)])
+def test_tile_tiny_periodic_meshes_bitwise(csw, cuda_stream, n, k):
+    """2 and 8 cells on a periodic square: a cell meets the same neighbour
+    across several faces (and itself across none), the periodic images give
+    normals that need not be exact negatives, and the whole mesh is one ragged
+    tile."""
+    for pb in (W.burgers_sine(n, seed=31), W.euler_entropy_wave(n, seed=32)):
+        s = csw.Solver(pb.equation, k, csw.FP64, csw.LIMITER_OFF, stream=cuda_stream)
+        s.setup(pb)
+        u = state(pb, k, 620 + n)
+        s.set_stage_shape(128, 0, 0)
+        ref = s.eval_rhs(u, 0.0)
+        for shape in TILE_SHAPES:
+            s.set_stage_shape(*shape)
+            assert np.array_equal(s.eval_rhs(u, 0.0), ref), shape
+        s.close()
+
