@@ -348,6 +348,12 @@ def run_ours(args):
     (s.read_modes_f32 if f32_io else s.read_modes)(host_in)
     write_fn, read_fn = (s.write_modes_f32, s.read_modes_f32) if f32_io else (s.write_modes, s.read_modes)
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    # warm-up through the same calls (first launches of the layout kernels, the step
+    # graph after an external state write), then the timed iterations
+    for _ in range(max(3, args.warmup)):
+        write_fn(host_in)
+        s.step(0.0, 1, NO_END)
+        read_fn(host_out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -594,7 +600,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dmr", choices=sorted(WORKLOADS))
     ap.add_argument("--profile-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--fp32-steps", type=int, default=2000)
     ap.add_argument("--adjoint-steps", type=int, default=100)
