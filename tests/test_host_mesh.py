@@ -105,3 +105,32 @@ def test_morton_order_keeps_neighbours_close(cswdg):
     same = np.concatenate([(nbr[f][m] // 256) == (c[m] // 256) for f, m in enumerate(inner)])
     dist = np.concatenate([np.abs(nbr[f][m] - c[m]) for f, m in enumerate(inner)])
     assert same.mean() > 0.85 and np.median(dist) <= 8, (same.mean(), np.median(dist))
+
+
+def test_tile_face_counts_of_the_flop_model(cswdg):
+    """The per-variant FP64 flop count of bench.py (host logic only): k_stage's
+    fixed count; for k_stage_tiles a brute-force walk over the tiles' faces
+    (each interior face once, each face to another tile or the boundary once
+    per side) gives the same flux and outer-trace counts, and the count lies
+    between its bounds (one flux per face pair at the least, k_stage's three at
+    the most)."""
+    import bench
+    pb = W.double_mach(40, 10, seed=3)
+    nbr = cswdg.host_mesh(pb, 2)["nbr"]
+    nc = nbr.shape[1]
+    assert bench.stage_flops_per_cell(cswdg, pb, (128, 0, 0)) == bench.STAGE_FLOPS_PER_CELL_EULER_P2
+    for blk in (128, 256):
+        flux = outer = 0
+        for c in range(nc):
+            for f in range(3):
+                n = int(nbr[f, c])
+                if n >= 0 and n // blk == c // blk and n != c:
+                    flux += 1 if c < n else 0
+                else:
+                    flux += 1
+                    outer += 1 if n >= 0 else 0
+        want = 7 * 147 + 12 * (40 + 52) + 4 * (flux / nc) * 67 + 4 * (outer / nc) * 40 + 120 + 110
+        got = bench.stage_flops_per_cell(cswdg, pb, (blk, 0, 1))
+        assert abs(got - want) < 1e-9 * want
+        lo = 7 * 147 + 12 * (40 + 52) + 4 * 1.5 * 67 + 230
+        assert lo <= got < bench.STAGE_FLOPS_PER_CELL_EULER_P2
